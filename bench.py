@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 exact triangle counter.
+
+One step = one pass of the whole path over the workload's edge list: build (canonical
+keys, radix sort, dedupe, degrees, orientation, N+ lists, tasks) and count (cost prefix,
+Eq. 1 / Eq. 2 schedule, persistent intersection kernel, exact reduction), through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cl|ba|er] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  `value` is oriented edges (distinct undirected edges) per
+second over all ranks with the edge list resident in HBM when the timed region starts;
+`e2e` is the same metric with the edge list in pinned host memory, copies included.
+With N > 1 every rank counts its own replica of the workload (replicas only: the
+counts need no exchange), so the scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "exact oriented-edges/s per GB300"
+UNIT = "oriented-edges/s"
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD_TEXT = {
+    "cl": "chung-lu n=10,000,000 exponent 2.1 mean degree 40 w0=1e5, 2.0e8 edge draws, seed 2",
+    "ba": "barabasi-albert n=1,000,000 k=50 (avg degree 100), seed 1",
+    "er": "erdos-renyi G(n=10,000, m=100,000), seed 0",
+}
+# input pairs of the same workload the oracle counts per CPU-baseline run (about 10-30 s)
+CPU_SAMPLE_PAIRS = {"cl": 32_000_000, "ba": 16_000_000, "er": 100_000}
+# input pairs per step of the reference (oracle) arm, so that --steps K --warmup W ends in minutes
+REF_SAMPLE_PAIRS = {"cl": 4_000_000, "ba": 2_000_000, "er": 100_000}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--workload", default="cl", choices=["cl", "ba", "er"])
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while running (start before, stop after the timed region)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str | None):
+        self.lines = []
+        self.proc = None
+        self.gpu_index = gpu_index
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_index is not None:
+            cmd += ["-i", self.gpu_index]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- helpers
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def count_kernel_source_hash():
+    with open(os.path.join(ROOT, "paper_1406_5687_gb300", "csrc", "count.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def stored_traffic(workload):
+    """DRAM bytes per launch of the count kernel from a committed ncu summary, if it is
+    still about the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"k_count_{workload}_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    if rec.get("count_cu_sha256") != count_kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(g, piece):
+    """Bytes the count kernel must move per launch if nothing were cached:
+    every task reads its 16-byte record and streams its partner list once per piece of
+    its owner's list (4 B per entry); every owner stages its own list once (4 B per entry)
+    and reads its two offsets (16 B).  Also returns the merge-model figure
+    4 (sum_{(v,u)} |N+(u)| + m_hat) + 16 n of the paper's direction of Fig. 1."""
+    import numpy as np
+    deg, off, cols, tasks = g.csr()
+    off = off.cpu().numpy()
+    t = tasks.cpu().numpy()
+    dh = np.diff(off)
+    owner = t[:, 0].astype(np.int64)
+    plen = t[:, 3].astype(np.int64)
+    pieces = (dh[owner] + piece - 1) // piece
+    streamed = int((pieces * plen).sum()) * 4
+    owners = np.unique(owner)
+    staged = int(dh[owners].sum()) * 4
+    b_alg = streamed + staged + 16 * len(t) + 16 * len(owners)
+    info = g.info()
+    b_merge = 4 * (int(info["sum_dhat_u"]) + int(info["m_hat"])) + 16 * int(info["n"])
+    return b_alg, b_merge, {"streamed_entries": int((pieces * plen).sum()), "owners": int(len(owners)),
+                            "tasks": int(len(t))}
+
+
+def cpu_baseline(workload, pairs, threads=1):
+    """The oracle as it stands (simple graph, Fig. 1 lists, Fig. 1 count) on the first
+    `pairs` input pairs of the workload, timed on the host."""
+    import oracle
+    from graphgen import workloads as W
+    spec = W.SINGLE[workload]
+    if spec.family == "cl":
+        import dataclasses
+        s, d = dataclasses.replace(spec, draws=min(pairs, spec.draws)).edges()
+    else:
+        s, d = spec.edges()
+        s, d = s[:pairs], d[:pairs]
+    t0 = time.perf_counter()
+    csr = oracle.oriented_csr(oracle.simple_graph(spec.n, s, d))
+    T = oracle.count(csr, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": csr.m_hat / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {len(s):,} input pairs of the workload ({csr.m_hat:,} distinct edges, {T:,} triangles), "
+                      f"oracle end to end (simple graph, Fig. 1 lists, Fig. 1 count), {dt:.2f} s"}
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    from graphgen import workloads as W
+    spec = W.SINGLE[args.workload]
+    pairs = REF_SAMPLE_PAIRS[args.workload]
+    if spec.family == "cl":
+        import dataclasses
+        s, d = dataclasses.replace(spec, draws=min(pairs, spec.draws)).edges()
+    else:
+        s, d = spec.edges()
+        s, d = s[:pairs], d[:pairs]
+    times, mh = [], 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        csr = oracle.oriented_csr(oracle.simple_graph(spec.n, s, d))
+        oracle.count(csr)
+        dt = time.perf_counter() - t0
+        mh = csr.m_hat
+        if i >= args.warmup:
+            times.append(dt)
+    mean = sum(times) / len(times)
+    value = mh / mean
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload], "sample_pairs": len(s), "m_hat": mh},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {len(s):,} input pairs of the workload per step, "
+                                       "oracle end to end, single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank, world, local):
+    import numpy as np
+    import torch
+    import paper_1406_5687_gb300 as tc
+    from graphgen import workloads as W
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    spec = W.SINGLE[args.workload]
+    s, d = spec.edges()
+    m_in = len(s)
+    s_pin = torch.from_numpy(s).pin_memory()
+    d_pin = torch.from_numpy(d).pin_memory()
+    del s, d
+    s_dev, d_dev = s_pin.cuda(), d_pin.cuda()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    opt = tc.default_options()
+    g = tc.Graph.build(s_dev, d_dev, spec.n, opt)
+    info = g.info()
+    T_ref = g.count()
+    b_alg, b_merge, work = algorithmic_bytes(g, opt.piece)
+    g.free()
+    m_hat = info["m_hat"]
+
+    def device_step():
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        gg = tc.Graph.build(s_dev, d_dev, spec.n, opt)
+        e1.record(stream)
+        T, meta, _, _ = gg.count_ex(timing=True)
+        e2.record(stream)
+        e2.synchronize()
+        gg.free()
+        if T != T_ref:
+            raise RuntimeError(f"count changed between steps: {T} != {T_ref}")
+        return e0.elapsed_time(e2), e0.elapsed_time(e1), e1.elapsed_time(e2), meta["kernel_ms"], meta["prefix_ms"]
+
+    for _ in range(args.warmup):
+        device_step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get(
+        "CUDA_VISIBLE_DEVICES") else str(local)
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    l0 = tc.kernel_launches()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    steps = [device_step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = tc.kernel_launches() - l0
+    clk = clocks.stop()
+    total_ms = sum(x[0] for x in steps)
+    if pg:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+        pg.barrier()
+    value = world * args.steps * m_hat / (total_ms / 1e3)
+    build_ms = statistics.mean(x[1] for x in steps)
+    count_ms = statistics.mean(x[2] for x in steps)
+    kernel_ms = statistics.mean(x[3] for x in steps)
+    prefix_ms = statistics.mean(x[4] for x in steps)
+
+    # e2e: edge list in pinned host memory, copies and the 8-byte result read inside the step
+    e2e = None
+    if not args.no_e2e:
+        def host_step():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gg = tc.Graph.build(s_pin, d_pin, spec.n, opt)
+            T = gg.count()
+            e1.record(stream)
+            e1.synchronize()
+            gg.free()
+            if T != T_ref:
+                raise RuntimeError("count changed in the e2e run")
+            return e0.elapsed_time(e1)
+        host_step()
+        e2e_ms = sum(host_step() for _ in range(args.steps))
+        if pg:
+            t = torch.tensor([e2e_ms], dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * args.steps * m_hat / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * m_in, "d2h_bytes_per_step": 8,
+               "ms_per_step": e2e_ms / args.steps}
+
+    peak, peak_kind = measured_peaks()
+    achieved = b_alg / (kernel_ms / 1e3) / 1e9
+    roofline = {"kernel": "k_count (persistent intersection, steps a7-a8)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"hbm_gbs of {peak_kind}", "traffic": stored_traffic(args.workload),
+                "algorithmic_bytes": b_alg, "launch_ms": kernel_ms,
+                "merge_model_bytes": b_merge, "merge_model_gbs": b_merge / (kernel_ms / 1e3) / 1e9}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, CPU_SAMPLE_PAIRS[args.workload])
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": WORKLOAD_TEXT[args.workload], "m_input": m_in, "m_hat": m_hat,
+                           "n": info["n"], "triangles": T_ref, "tasks": info["tasks"],
+                           "max_degree": info["max_degree"], "max_dhat": info["max_dhat"],
+                           "l2": "inputs larger than L2 (edge list, lists and tasks each exceed 129 MB)",
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "options": {"piece": opt.piece, "warps_per_block": opt.warps_per_block,
+                                       "cost_model": "edge", "static_percent": opt.static_percent}},
+                "phases_ms": {"build": build_ms, "count": count_ms, "count_prefix": prefix_ms,
+                              "count_kernel": kernel_ms},
+                "count_only": {"value": m_hat / (count_ms / 1e3), "unit": UNIT,
+                               "note": "m_hat / (cost prefix + schedule + intersection), lists resident"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "work": work, "wall_s_timed": t_wall}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,339 @@
+/*
+ * tc.h -- C ABI of the GB300 exact triangle counter.
+ *
+ * Method: the degree-ordered node-iterator of Arifuzzaman, Khan and Marathe,
+ * "Parallel Algorithms for Counting Triangles in Networks with Large Degrees"
+ * (arXiv 1406.5687), Fig. 1, with the cost-balanced dynamic load balancing of
+ * Sec. V (Eq. 1 and Eq. 2), run as CUDA kernels on one sm_103a GPU.
+ *
+ * Conventions for every call:
+ *   - Vertex ids are int32 in [0, n).  Counts are exact uint64.
+ *   - Pointers marked "host or device" may point to either; the library asks the
+ *     CUDA runtime which.  Pointers marked "device" must be device memory of the
+ *     current device.  Pointers marked "host" must be host memory.
+ *   - The caller owns every buffer it passes in; the library never frees or keeps
+ *     it after the call returns (unless stated).  The library owns the opaque
+ *     handles it returns and all device memory behind them until the matching
+ *     *_free / *_destroy call.
+ *   - Work is enqueued on `stream` (NULL = the legacy default stream).  Calls
+ *     that return results into host memory synchronise that stream.
+ *   - Errors are returned as tc_status, never thrown or printed.  When a kernel
+ *     detects a problem it sets a device error word; the first error wins and is
+ *     returned by the next call that synchronises.  No kernel traps or asserts.
+ *   - The device used is the current CUDA device at the call.
+ */
+#ifndef TC_H_
+#define TC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, declared without the CUDA headers. */
+typedef struct CUstream_st* tc_stream_t;
+
+typedef enum tc_status {
+    TC_OK = 0,
+    TC_ERR_INVALID_ARG = 1,   /* NULL/negative argument, bad option, or strict input policy saw a loop or repeat */
+    TC_ERR_VERTEX_RANGE = 2,  /* an input id outside [0, n) */
+    TC_ERR_OOM = 3,           /* a device or pinned-host allocation failed */
+    TC_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    TC_ERR_TIMEOUT = 5,       /* a bounded device wait or retry loop gave up */
+    TC_ERR_BUDGET = 6,        /* the request needs more device memory than the configured budget */
+    TC_ERR_UNSUPPORTED = 7    /* the input exceeds a limit of this build (e.g. n >= 2^31 - 1) */
+} tc_status;
+
+/* Static text for a status code (never NULL). */
+const char* tc_status_str(tc_status s);
+
+/* Library version string, e.g. "1.0.0 sm_103a". */
+const char* tc_version(void);
+
+/* ------------------------------------------------------------------ options */
+
+/*
+ * Cost of a task, used for the partition (step a6).  A task is one oriented edge,
+ * owned by the endpoint with the longer list.
+ *   TC_COST_EDGE    this build's model of its own work: pieces(owner) *
+ *                   (d^_partner + c_task), plus d^_owner + c_owner on the owner's
+ *                   last task (default);
+ *   TC_COST_MERGE   the paper's merge cost d^_v + d^_u of one edge (Sec. III-A);
+ *   TC_COST_ONE     f(v) = 1 (Sec. V-A), per owner vertex;
+ *   TC_COST_DEGREE  f(v) = d_v (Sec. V-A), per owner vertex;
+ *   TC_COST_PATRIC  f(v) = sum_{u in N_v} (d^_v + d^_u) (Sec. IV-B), per owner vertex;
+ *   TC_COST_NEW     f(v) = sum_{u in Nfull_v - N_v} (d^_v + d^_u) (Sec. IV-F), per owner.
+ * Per-vertex costs sit on the owner's last task, so a chunk never splits a vertex
+ * (the paper's atomic task <v,1>, Sec. V-A).  The cost changes speed, never the count.
+ */
+typedef enum tc_cost_model {
+    TC_COST_EDGE = 0,
+    TC_COST_MERGE = 1,
+    TC_COST_ONE = 2,
+    TC_COST_DEGREE = 3,
+    TC_COST_PATRIC = 4,
+    TC_COST_NEW = 5
+} tc_cost_model;
+
+/* Per-vertex cost functions for tc_vertex_cost (Sec. IV-B, IV-F, V-A). */
+typedef enum tc_cost_fn { TC_FN_ONE = 0, TC_FN_DEGREE = 1, TC_FN_PATRIC = 2, TC_FN_NEW = 3 } tc_cost_fn;
+
+/* Sec. II assumes a simple graph.  SANITIZE drops self-loops and merges repeated
+ * or reversed pairs; STRICT returns TC_ERR_INVALID_ARG if it sees any. */
+typedef enum tc_input_policy { TC_INPUT_SANITIZE = 0, TC_INPUT_STRICT = 1 } tc_input_policy;
+
+/*
+ * Optional device allocator.  alloc returns NULL on failure (the library then
+ * returns TC_ERR_OOM); release frees what alloc returned.  Both get the stream
+ * the memory is used on.  NULL hooks select cudaMallocAsync / cudaFreeAsync.
+ */
+typedef void* (*tc_alloc_fn)(void* ctx, size_t bytes, tc_stream_t stream);
+typedef void (*tc_release_fn)(void* ctx, void* ptr, tc_stream_t stream);
+
+typedef struct tc_options {
+    int32_t input_policy;      /* tc_input_policy */
+    int32_t cost_model;        /* tc_cost_model */
+    int32_t piece;             /* owner-list entries staged per shared-memory hash table: 256, 512 or 1024 (default 1024) */
+    int32_t warps_per_block;   /* workers per block of the count kernel: 4, 8 or 16 (default 8) */
+    int32_t blocks_per_sm;     /* resident blocks per SM of the count kernel (0 = as many as fit) */
+    int32_t static_percent;    /* share of the total cost handed out as initial tasks (Eq. 1); default 50 */
+    int64_t min_chunk;         /* floor of an Eq. 2 chunk, in cost units (0 = automatic) */
+    int32_t c_task;            /* TC_COST_EDGE per-task constant (default 4) */
+    int32_t c_owner;           /* TC_COST_EDGE per-owner constant (default 32) */
+    int64_t hbm_budget_bytes;  /* device memory a build may hold at its peak (0 = no limit) */
+    int64_t retry_limit;       /* bound on any device retry loop before TC_ERR_TIMEOUT (0 = default 1<<24) */
+    tc_alloc_fn alloc;         /* optional allocator hooks (both or neither) */
+    tc_release_fn release;
+    void* alloc_ctx;
+} tc_options;
+
+/* Fill *opt with the defaults listed above. */
+void tc_options_default(tc_options* opt);
+
+/* -------------------------------------------------------------- single graph */
+
+typedef struct tc_graph* tc_graph_t;
+
+/*
+ * Build the device representation of a graph (steps a1-a5 and the task array):
+ * canonical keys, radix sort, dedupe, degrees, orientation by the order of
+ * Sec. III-A, the N+ lists of Fig. 1 (sorted ascending), and the owner-grouped
+ * task array.
+ *   src, dst  host or device, m int32 each: edge i is (src[i], dst[i]); never modified.
+ *   m         number of input pairs (>= 0).
+ *   n         number of vertices, 0 <= n < 2^31 - 1.
+ *   opt       NULL for defaults; copied into the handle.
+ *   out       receives the handle; NULL on error.
+ * Errors: TC_ERR_INVALID_ARG (NULL pointers with m > 0, negative sizes, bad
+ * options, strict policy violated), TC_ERR_VERTEX_RANGE, TC_ERR_OOM,
+ * TC_ERR_BUDGET, TC_ERR_CUDA.  Synchronises `stream`.
+ */
+tc_status tc_build(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
+                   const tc_options* opt, tc_stream_t stream, tc_graph_t* out);
+
+/* Release a handle and its device memory (NULL-safe).  Waits for the stream of the
+ * handle's last call; the handle must not be in use on any other stream. */
+void tc_free(tc_graph_t g);
+
+/*
+ * Exact triangle count T = sum over oriented edges (v,u) of |N+(v) ∩ N+(u)|
+ * (Fig. 1; Sec. V's schedule; steps a6-a8).
+ *   total  host; receives T.
+ * Synchronises `stream`.  Errors: TC_ERR_INVALID_ARG, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_OOM.
+ */
+tc_status tc_count(tc_graph_t g, tc_stream_t stream, uint64_t* total);
+
+/*
+ * Same count, enqueued only: total_dev (device, one uint64) receives T when the
+ * stream reaches it.  Nothing is allocated after the handle's first count, so
+ * the call can be captured into a CUDA graph after one warm-up call.  Device-side
+ * errors are reported by tc_graph_check.
+ */
+tc_status tc_count_async(tc_graph_t g, tc_stream_t stream, uint64_t* total_dev);
+
+/* Synchronise `stream` and return (and clear) the handle's device error word. */
+tc_status tc_graph_check(tc_graph_t g, tc_stream_t stream);
+
+/*
+ * Per-vertex counts T_v (Sec. II): each triangle adds one to each of its three
+ * vertices, so sum T_v = 3T.
+ *   t_v    device, n uint64 (overwritten).
+ *   total  host (nullable); receives T.
+ */
+tc_status tc_count_per_vertex(tc_graph_t g, tc_stream_t stream, uint64_t* t_v, uint64_t* total);
+
+/*
+ * Per-oriented-edge counts: c[i] = |N+(v) ∩ N+(u)| for the oriented edge stored at
+ * position i of the N+ lists (tc_graph_csr); by Theorem 1 each triangle is counted
+ * on exactly one edge: the one joining its lowest and middle vertex.
+ *   c      device, m_hat uint32 (overwritten).
+ *   total  host (nullable); receives T.
+ */
+tc_status tc_count_per_edge(tc_graph_t g, tc_stream_t stream, uint32_t* c, uint64_t* total);
+
+/* Local clustering coefficients C_v = 2 T_v / (d_v (d_v - 1)), 0 when d_v < 2
+ * (the use named in Sec. I).  t_v: device, n uint64 from tc_count_per_vertex;
+ * cc: device, n double (overwritten). */
+tc_status tc_clustering(tc_graph_t g, const uint64_t* t_v, double* cc, tc_stream_t stream);
+
+/* ----------------------------------------------------------- introspection */
+
+typedef struct tc_graph_info {
+    int32_t n;
+    int32_t max_degree;    /* max d_v */
+    int32_t max_dhat;      /* max |N+(v)| (effective degree, Sec. III-A) */
+    int32_t id_bits;       /* bits per vertex id in the sort keys */
+    int64_t m_in;          /* input pairs */
+    int64_t self_loops;    /* dropped (sanitize) */
+    int64_t duplicates;    /* merged repeats, either orientation (sanitize) */
+    int64_t m_hat;         /* distinct undirected edges = oriented edges */
+    int64_t tasks;         /* oriented edges whose partner list is non-empty */
+    uint64_t sum_dhat_v;   /* sum over oriented edges (v,u) of d^_v */
+    uint64_t sum_dhat_u;   /* sum over oriented edges (v,u) of d^_u */
+    uint64_t sum_stream;   /* sum over tasks of d^_partner: list entries the count kernel streams (piece 1024) */
+    int64_t device_bytes;  /* device memory held by the handle */
+} tc_graph_info;
+
+tc_status tc_graph_get_info(tc_graph_t g, tc_graph_info* info);
+
+/*
+ * Device pointers to the handle's arrays (valid until tc_free; read-only):
+ *   deg   n int32          d_v
+ *   off   n+1 int64        N+(v) = cols[off[v] .. off[v+1])
+ *   cols  m_hat int32      ascending within each list
+ *   tasks 4*tasks uint32   one record per task, sorted by (owner, partner):
+ *                          owner, partner, start of N+(partner) in cols, |N+(partner)|
+ * Any output pointer may be NULL.
+ */
+tc_status tc_graph_csr(tc_graph_t g, const int32_t** deg, const int64_t** off, const int32_t** cols,
+                       const uint32_t** tasks);
+
+/*
+ * Per-vertex cost f(v) (step a6): fn is a tc_cost_fn.
+ *   f  device, n uint64 (overwritten).
+ */
+tc_status tc_vertex_cost(tc_graph_t g, int32_t fn, tc_stream_t stream, uint64_t* f);
+
+/*
+ * Count with explicit options and a record of the schedule (steps a6-a8).
+ *   opt      NULL = the handle's options; only the count fields are used.
+ *   total    host; receives T.
+ *   trace    NULL, or a record the count fills in:
+ *              chunks  device, 4*cap uint64 or NULL: one record per chunk a worker
+ *                      took, (cost_lo, cost_hi, task_lo, task_hi), in no
+ *                      particular order; records beyond cap are dropped;
+ *              workers_busy device, 2*W uint64 or NULL: per worker, (clock64
+ *                      cycles spent on tasks, chunks taken) -- the per-worker
+ *                      idle time of Sec. V-E;
+ *            and on return: n_chunks (records produced), n_workers (W),
+ *            total_cost (C), min_chunk (the Eq. 2 floor used), prefix_ms and
+ *            kernel_ms (CUDA events recorded on `stream` around the two phases).
+ * With trace != NULL the call synchronises `stream` before returning.
+ */
+typedef struct tc_count_trace {
+    uint64_t* chunks;
+    int64_t cap;
+    uint64_t* workers_busy;
+    int64_t n_chunks;
+    int64_t n_workers;
+    uint64_t total_cost;
+    uint64_t min_chunk;
+    float prefix_ms;   /* out: CUDA-event time of the cost prefix and schedule set-up (a6) */
+    float kernel_ms;   /* out: CUDA-event time of the persistent intersection kernel (a7-a8) */
+} tc_count_trace;
+
+tc_status tc_count_ex(tc_graph_t g, const tc_options* opt, tc_stream_t stream, uint64_t* total,
+                      tc_count_trace* trace);
+
+/* Number of kernels this library has launched in this process so far (all devices,
+ * all handles); differences around a region count the launches inside it. */
+int64_t tc_kernel_launches(void);
+
+/* ------------------------------------------------------------------ batch */
+
+typedef struct tc_batch* tc_batch_t;
+
+/*
+ * Batched counting: k built graphs counted by one persistent launch.  Their task
+ * arrays are addressed through a device table of per-graph descriptors with
+ * int64 offsets; one global chunk schedule (Eq. 1 + Eq. 2) spans every graph's
+ * tasks, and each chunk adds into its own graph's total.  The launch sequence is
+ * captured once into a CUDA graph and replayed by tc_batch_run.
+ *   graphs  host array of k handles (kept referenced, not owned: free the batch
+ *           before any of its graphs).
+ */
+tc_status tc_batch_create(const tc_graph_t* graphs, int32_t k, const tc_options* opt,
+                          tc_stream_t stream, tc_batch_t* out);
+
+/* Replay the captured launch; totals_dev: device, k uint64 (overwritten). */
+tc_status tc_batch_run(tc_batch_t b, tc_stream_t stream, uint64_t* totals_dev);
+
+void tc_batch_free(tc_batch_t b);
+
+/* Convenience: create, run once, copy the k totals to host memory, free. */
+tc_status tc_batch_count(const tc_graph_t* graphs, int32_t k, tc_stream_t stream, uint64_t* totals);
+
+/*
+ * Batched build: k edge lists (host memory) built into k handles through one
+ * packed pipeline (one sort over graph-tagged keys).
+ *   src, dst   host arrays of k pointers to int32 edge arrays (host memory).
+ *   m, n       host arrays of k sizes.
+ *   out        host array of k handles (each freed with tc_free).
+ */
+tc_status tc_build_batch(const int32_t* const* src, const int32_t* const* dst, const int64_t* m,
+                         const int32_t* n, int32_t k, const tc_options* opt, tc_stream_t stream,
+                         tc_graph_t* out);
+
+/* ---------------------------------------------------------------- serving */
+
+typedef struct tc_server* tc_server_t;
+
+typedef struct tc_result {
+    uint64_t tag;       /* the caller's tag from tc_server_submit */
+    uint64_t total;     /* T */
+    int32_t status;     /* tc_status of this request */
+    int32_t slot;       /* the execution slot that ran it */
+    double t_submit;    /* seconds (steady clock) when submitted */
+    double t_start;     /* when admitted to a slot */
+    double t_done;      /* when the result was known on the host */
+} tc_result;
+
+/*
+ * A request loop with continuous batching: submitted edge lists wait in a host
+ * queue; a scheduler thread admits them to one of `slots` execution slots (each
+ * with its own CUDA stream) as soon as a slot is free and the device memory of
+ * the requests in flight stays within hbm_budget_bytes; builds and counts of
+ * different slots overlap on the device.  The CSR of a finished request is
+ * released as soon as its result is read back.
+ *   hbm_budget_bytes  > 0.
+ *   slots             1..64.
+ *   opt               NULL = defaults.
+ */
+tc_status tc_server_create(int64_t hbm_budget_bytes, int32_t slots, const tc_options* opt,
+                           tc_server_t* out);
+
+/*
+ * Queue one graph.  src/dst: host, m int32 each; the server copies them before
+ * returning, so the caller may reuse them.  Errors: TC_ERR_INVALID_ARG,
+ * TC_ERR_BUDGET (the graph alone needs more than the budget), TC_ERR_OOM.
+ */
+tc_status tc_server_submit(tc_server_t s, const int32_t* src, const int32_t* dst, int64_t m,
+                           int32_t n, uint64_t tag);
+
+/* Move up to max finished results into out (host); *n_out receives how many. */
+tc_status tc_server_poll(tc_server_t s, tc_result* out, int32_t max, int32_t* n_out);
+
+/* Block until every submitted request has finished or timeout_ms passes
+ * (TC_ERR_TIMEOUT). */
+tc_status tc_server_drain(tc_server_t s, int64_t timeout_ms);
+
+/* Stop the scheduler, wait for in-flight work, release everything (NULL-safe). */
+void tc_server_destroy(tc_server_t s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H_ */

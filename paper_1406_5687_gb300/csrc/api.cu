@@ -1,0 +1,299 @@
+// api.cu -- the extern "C" entry points for single graphs declared in include/tc.h.
+#include <climits>
+#include <cstring>
+#include <new>
+
+#include "graph.cuh"
+#include "primitives.cuh"
+
+namespace tcg {
+
+// Small per-handle device block: error word, last result, schedule state.
+struct HandleDev {
+    DevStatus status;
+    unsigned long long result;
+    long long pad;
+    Sched sched;
+};
+
+tc_status check_options(const tc_options& o) {
+    if (o.input_policy != TC_INPUT_SANITIZE && o.input_policy != TC_INPUT_STRICT) return TC_ERR_INVALID_ARG;
+    if (o.cost_model < TC_COST_EDGE || o.cost_model > TC_COST_NEW) return TC_ERR_INVALID_ARG;
+    if (o.piece != 128 && o.piece != 256 && o.piece != 512 && o.piece != 1024 && o.piece != 2048)
+        return TC_ERR_INVALID_ARG;
+    if (o.warps_per_block != 1 && o.warps_per_block != 2 && o.warps_per_block != 4 && o.warps_per_block != 8 &&
+        o.warps_per_block != 16)
+        return TC_ERR_INVALID_ARG;
+    if ((size_t)o.warps_per_block * 2 * o.piece * 4 > 200 * 1024) return TC_ERR_INVALID_ARG;  // shared memory per block
+    if (o.blocks_per_sm < 0 || o.static_percent < 0 || o.static_percent > 100) return TC_ERR_INVALID_ARG;
+    if (o.min_chunk < 0 || o.c_task < 0 || o.c_owner < 0 || o.hbm_budget_bytes < 0 || o.retry_limit < 0)
+        return TC_ERR_INVALID_ARG;
+    if ((o.alloc == nullptr) != (o.release == nullptr)) return TC_ERR_INVALID_ARG;
+    return TC_OK;
+}
+
+static bool is_device_pointer(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device bytes a build of (m, n) holds at its peak (keys, sort scratch, arrays, staging).
+int64_t build_peak_bytes(int64_t m, int32_t n, bool host_input) {
+    int64_t mm = m > 0 ? m : 1;
+    int64_t b = 16 * mm + radix_sort_scratch_bytes(mm) + 8 * (int64_t)n * 2 + 8 * ((int64_t)n + 1) + 4 * mm +
+                16 * mm + (1 << 20);
+    if (host_input) b += 8 * mm;
+    return b;
+}
+
+// Device bytes a built graph keeps, including the count workspace.
+int64_t graph_resident_bytes(int64_t m_hat, int64_t tasks, int32_t n) {
+    return 4 * (int64_t)n + 8 * ((int64_t)n + 1) + 4 * m_hat + 16 * tasks + 8 * (tasks + 1) +
+           8 * (tasks / 2048 + 64) + 8 * (int64_t)n + (1 << 16);
+}
+
+static void free_graph(tc_graph* g) {
+    if (!g) return;
+    cudaStream_t s = g->last_stream;
+    cudaStreamSynchronize(s);
+    auto put = [&](void* p, size_t bytes) {
+        if (p) g->al.put(p, bytes, s);
+    };
+    put(g->deg, (size_t)(g->n > 0 ? g->n : 1) * 4);
+    put(g->off, ((size_t)g->n + 1) * 8);
+    put(g->cols, (size_t)(g->m_hat > 0 ? g->m_hat : 1) * 4);
+    put(g->trec, (size_t)(g->tasks > 0 ? g->tasks : 1) * sizeof(TaskRec));
+    put(g->work.prefix, (size_t)(g->tasks + 1) * 8);
+    put(g->work.scan_scr, (size_t)g->work.scan_words * 8);
+    put(g->work.fcost, (size_t)(g->n > 0 ? g->n : 1) * 8);
+    put(g->status, sizeof(HandleDev));
+    cudaStreamSynchronize(s);
+    delete g;
+}
+
+static tc_status read_status(tc_graph* g, cudaStream_t s, unsigned long long* result) {
+    HandleDev h;
+    TC_CUDA_TRY(cudaMemcpyAsync(&h, g->status, offsetof(HandleDev, pad), cudaMemcpyDeviceToHost, s));
+    TC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (result) *result = h.result;
+    if (h.status.code != 0) {
+        TC_CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(DevStatus), s));
+        TC_CUDA_TRY(cudaStreamSynchronize(s));
+        return (tc_status)h.status.code;
+    }
+    return TC_OK;
+}
+
+}  // namespace tcg
+
+using namespace tcg;
+
+extern "C" {
+
+const char* tc_status_str(tc_status s) {
+    switch (s) {
+        case TC_OK: return "ok";
+        case TC_ERR_INVALID_ARG: return "invalid argument";
+        case TC_ERR_VERTEX_RANGE: return "vertex id outside [0, n)";
+        case TC_ERR_OOM: return "out of memory";
+        case TC_ERR_CUDA: return "CUDA runtime error";
+        case TC_ERR_TIMEOUT: return "bounded device wait gave up";
+        case TC_ERR_BUDGET: return "device memory budget exceeded";
+        case TC_ERR_UNSUPPORTED: return "input exceeds a limit of this build";
+    }
+    return "unknown status";
+}
+
+const char* tc_version(void) { return "1.0.0 sm_103a"; }
+
+void tc_options_default(tc_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->input_policy = TC_INPUT_SANITIZE;
+    o->cost_model = TC_COST_EDGE;
+    o->piece = 1024;
+    o->warps_per_block = 8;
+    o->blocks_per_sm = 0;
+    o->static_percent = 50;
+    o->min_chunk = 0;
+    o->c_task = 4;
+    o->c_owner = 32;
+    o->hbm_budget_bytes = 0;
+    o->retry_limit = 0;
+}
+
+tc_status tc_build(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, const tc_options* opt,
+                   tc_stream_t stream, tc_graph_t* out) {
+    if (!out) return TC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (m < 0 || n < 0 || n == INT32_MAX) return m < 0 || n < 0 ? TC_ERR_INVALID_ARG : TC_ERR_UNSUPPORTED;
+    if (m > 0 && (!src || !dst)) return TC_ERR_INVALID_ARG;
+    tc_options o;
+    tc_options_default(&o);
+    if (opt) o = *opt;
+    TC_TRY(check_options(o));
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool dev_in = m > 0 && is_device_pointer(src) && is_device_pointer(dst);
+    const bool mixed = m > 0 && (is_device_pointer(src) != is_device_pointer(dst));
+    if (mixed) return TC_ERR_INVALID_ARG;
+    if (o.hbm_budget_bytes > 0 && build_peak_bytes(m, n, !dev_in) > o.hbm_budget_bytes) return TC_ERR_BUDGET;
+
+    retain_pool_memory();
+    tc_graph* g = new (std::nothrow) tc_graph();
+    if (!g) return TC_ERR_OOM;
+    g->opt = o;
+    g->al.alloc = o.alloc;
+    g->al.release = o.release;
+    g->al.ctx = o.alloc_ctx;
+    g->al.budget = o.hbm_budget_bytes;
+    g->last_stream = s;
+    cudaGetDevice(&g->device);
+    tc_status st = TC_OK;
+    {
+        void* p = nullptr;
+        st = g->al.get(&p, sizeof(HandleDev), s);
+        if (st == TC_OK) {
+            g->status = (DevStatus*)p;
+            HandleDev* hd = (HandleDev*)p;
+            g->work.result = &hd->result;
+            g->work.sched = &hd->sched;
+            if (cudaMemsetAsync(p, 0, sizeof(HandleDev), s) != cudaSuccess) st = TC_ERR_CUDA;
+        }
+    }
+    if (st == TC_OK) {
+        const int32_t* s_d = src;
+        const int32_t* d_d = dst;
+        DevBuf<int32_t> ss, dd;
+        if (m > 0 && !dev_in) {
+            st = ss.alloc(&g->al, (size_t)m, s);
+            if (st == TC_OK) st = dd.alloc(&g->al, (size_t)m, s);
+            if (st == TC_OK && (cudaMemcpyAsync(ss.ptr, src, (size_t)m * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                                cudaMemcpyAsync(dd.ptr, dst, (size_t)m * 4, cudaMemcpyHostToDevice, s) != cudaSuccess))
+                st = TC_ERR_CUDA;
+            s_d = ss.ptr;
+            d_d = dd.ptr;
+        }
+        if (st == TC_OK) st = build_graph(g, s_d, d_d, m, n, s);
+    }
+    if (st != TC_OK) {
+        (void)cudaGetLastError();
+        free_graph(g);
+        return st;
+    }
+    *out = g;
+    return TC_OK;
+}
+
+void tc_free(tc_graph_t g) { free_graph(g); }
+
+tc_status tc_count(tc_graph_t g, tc_stream_t stream, uint64_t* total) {
+    if (!g || !total) return TC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last_stream = s;
+    TC_TRY(count_enqueue(g, g->opt, s, g->work.result, nullptr, nullptr, nullptr));
+    unsigned long long r = 0;
+    TC_TRY(read_status(g, s, &r));
+    *total = r;
+    return TC_OK;
+}
+
+tc_status tc_count_async(tc_graph_t g, tc_stream_t stream, uint64_t* total_dev) {
+    if (!g || !total_dev) return TC_ERR_INVALID_ARG;
+    g->last_stream = (cudaStream_t)stream;
+    return count_enqueue(g, g->opt, (cudaStream_t)stream, (unsigned long long*)total_dev, nullptr, nullptr, nullptr);
+}
+
+tc_status tc_graph_check(tc_graph_t g, tc_stream_t stream) {
+    if (!g) return TC_ERR_INVALID_ARG;
+    return read_status(g, (cudaStream_t)stream, nullptr);
+}
+
+tc_status tc_count_per_vertex(tc_graph_t g, tc_stream_t stream, uint64_t* t_v, uint64_t* total) {
+    if (!g || (!t_v && g->n > 0)) return TC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last_stream = s;
+    unsigned long long* tv = (unsigned long long*)t_v;
+    if (g->n > 0) TC_CUDA_TRY(cudaMemsetAsync(tv, 0, sizeof(uint64_t) * g->n, s));
+    TC_TRY(count_enqueue(g, g->opt, s, g->work.result, tv ? tv : nullptr, nullptr, nullptr));
+    unsigned long long r = 0;
+    TC_TRY(read_status(g, s, &r));
+    if (total) *total = r;
+    return TC_OK;
+}
+
+tc_status tc_count_per_edge(tc_graph_t g, tc_stream_t stream, uint32_t* c, uint64_t* total) {
+    if (!g || (!c && g->m_hat > 0)) return TC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last_stream = s;
+    if (g->m_hat > 0) TC_CUDA_TRY(cudaMemsetAsync(c, 0, sizeof(uint32_t) * g->m_hat, s));
+    TC_TRY(count_enqueue(g, g->opt, s, g->work.result, nullptr, c, nullptr));
+    unsigned long long r = 0;
+    TC_TRY(read_status(g, s, &r));
+    if (total) *total = r;
+    return TC_OK;
+}
+
+tc_status tc_clustering(tc_graph_t g, const uint64_t* t_v, double* cc, tc_stream_t stream) {
+    if (!g || ((!t_v || !cc) && g->n > 0)) return TC_ERR_INVALID_ARG;
+    g->last_stream = (cudaStream_t)stream;
+    return clustering_enqueue(g, t_v, cc, (cudaStream_t)stream);
+}
+
+tc_status tc_graph_get_info(tc_graph_t g, tc_graph_info* info) {
+    if (!g || !info) return TC_ERR_INVALID_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->n = g->n;
+    info->max_degree = g->max_degree;
+    info->max_dhat = g->max_dhat;
+    info->id_bits = g->id_bits;
+    info->m_in = g->m_in;
+    info->self_loops = g->self_loops;
+    info->duplicates = g->duplicates;
+    info->m_hat = g->m_hat;
+    info->tasks = g->tasks;
+    info->sum_dhat_v = g->sum_dhat_v;
+    info->sum_dhat_u = g->sum_dhat_u;
+    info->sum_stream = g->sum_stream;
+    info->device_bytes = g->bytes;
+    return TC_OK;
+}
+
+tc_status tc_graph_csr(tc_graph_t g, const int32_t** deg, const int64_t** off, const int32_t** cols,
+                       const uint32_t** tasks) {
+    if (!g) return TC_ERR_INVALID_ARG;
+    if (deg) *deg = g->deg;
+    if (off) *off = g->off;
+    if (cols) *cols = g->cols;
+    if (tasks) *tasks = (const uint32_t*)g->trec;
+    return TC_OK;
+}
+
+tc_status tc_vertex_cost(tc_graph_t g, int32_t fn, tc_stream_t stream, uint64_t* f) {
+    if (!g || (!f && g->n > 0)) return TC_ERR_INVALID_ARG;
+    g->last_stream = (cudaStream_t)stream;
+    return vertex_cost_enqueue(g, fn, (cudaStream_t)stream, f);
+}
+
+tc_status tc_count_ex(tc_graph_t g, const tc_options* opt, tc_stream_t stream, uint64_t* total,
+                      tc_count_trace* trace) {
+    if (!g || !total) return TC_ERR_INVALID_ARG;
+    tc_options o = opt ? *opt : g->opt;
+    TC_TRY(check_options(o));
+    if (trace && trace->cap < 0) return TC_ERR_INVALID_ARG;
+    if (trace && trace->cap > 0 && !trace->chunks) return TC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last_stream = s;
+    TC_TRY(count_enqueue(g, o, s, g->work.result, nullptr, nullptr, trace));
+    unsigned long long r = 0;
+    TC_TRY(read_status(g, s, &r));
+    *total = r;
+    return TC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,398 @@
+// build.cu -- steps a1-a5 of the path plus the task array.
+//
+//   a1  canonical keys (min << b) | max, ids range-checked, self-loops to a sentinel (Sec. II)
+//   a2  LSD radix sort, drop repeated keys -> the m_hat distinct edges (Sec. II)
+//   a3  degrees d_v
+//   a4  orientation by the order of Sec. III-A: u < v iff d_u < d_v or (d_u = d_v and u < v)
+//   a5  N+ lists (Fig. 1): sort the oriented keys, effective degrees, offsets, columns
+//   tasks: each oriented edge owned by the endpoint with the longer list; tasks whose
+//       partner list is empty are dropped; sorted by (owner, partner); 16-byte records.
+#include <climits>
+
+#include "graph.cuh"
+#include "primitives.cuh"
+#include "scan.cuh"
+
+namespace tcg {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(int64_t n, int threads = kThreads) {
+    int64_t g = ceil_div(n > 0 ? n : 1, threads);
+    return (unsigned)(g > 0x7FFFFFFF ? 0x7FFFFFFF : g);
+}
+
+// --------------------------------------------------------------------------- compaction
+constexpr int kCpItems = 8;
+constexpr int kCpBlock = 256;
+constexpr int64_t kCpTile = (int64_t)kCpBlock * kCpItems;
+
+template <class Pred>
+__global__ void __launch_bounds__(kCpBlock) k_compact_counts(Pred p, int64_t n, uint32_t* tile_counts) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kCpTile + (int64_t)warp * 32 * kCpItems;
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kCpItems; ++k) {
+        int64_t i = base + k * 32 + lane;
+        c += __popc(__ballot_sync(kFull, i < n && p(i)));
+    }
+    __shared__ uint32_t ws[kCpBlock / 32];
+    if (lane == 0) ws[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kCpBlock / 32; ++w) t += ws[w];
+        tile_counts[blockIdx.x] = t;
+    }
+}
+
+template <class Pred, class Val, class OutT>
+__global__ void __launch_bounds__(kCpBlock) k_compact_write(Pred p, Val v, int64_t n, const uint64_t* tile_prefix,
+                                                            OutT* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kCpTile + (int64_t)warp * 32 * kCpItems;
+    unsigned bal[kCpItems];
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kCpItems; ++k) {
+        int64_t i = base + k * 32 + lane;
+        bal[k] = __ballot_sync(kFull, i < n && p(i));
+        c += __popc(bal[k]);
+    }
+    __shared__ uint32_t ws[kCpBlock / 32];
+    if (lane == 0) ws[warp] = c;
+    __syncthreads();
+    uint64_t pos = tile_prefix[blockIdx.x];
+    for (int w = 0; w < warp; ++w) pos += ws[w];
+#pragma unroll
+    for (int k = 0; k < kCpItems; ++k) {
+        int64_t i = base + k * 32 + lane;
+        if ((bal[k] >> lane) & 1u) out[pos + __popc(bal[k] & lanemask_lt())] = v(i);
+        pos += __popc(bal[k]);
+    }
+}
+
+struct IdentityU32Scan {
+    const uint32_t* v;
+    __device__ uint64_t operator()(int64_t i) const { return v[i]; }
+};
+
+// Compacts {v(i) : p(i)} in index order into out.  *count_dev receives the count (device,
+// inside `prefix_out` at [ntiles]); returns the device address of that count.
+template <class Pred, class Val, class OutT>
+tc_status compact(Pred p, Val v, int64_t n, OutT* out, Allocator* al, cudaStream_t s, uint64_t* count_host) {
+    const int64_t tiles = ceil_div(n > 0 ? n : 1, kCpTile);
+    DevBuf<uint32_t> tc;
+    DevBuf<uint64_t> tp, scr;
+    TC_TRY(tc.alloc(al, tiles, s));
+    TC_TRY(tp.alloc(al, tiles + 1, s));
+    TC_TRY(scr.alloc(al, scan_scratch_words(tiles), s));
+    if (n > 0) {
+        k_compact_counts<<<(unsigned)tiles, kCpBlock, 0, s>>>(p, n, tc.ptr);
+        note_launch();
+        TC_CUDA_TRY(scan_exclusive(IdentityU32Scan{tc.ptr}, tiles, tp.ptr, scr.ptr, s));
+        k_compact_write<<<(unsigned)tiles, kCpBlock, 0, s>>>(p, v, n, tp.ptr, out);
+        note_launch();
+        TC_CUDA_TRY(cudaGetLastError());
+        TC_CUDA_TRY(cudaMemcpyAsync(count_host, tp.ptr + tiles, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        TC_CUDA_TRY(cudaStreamSynchronize(s));
+    } else {
+        *count_host = 0;
+    }
+    return TC_OK;
+}
+
+// --------------------------------------------------------------------------- a1: canonical keys
+__global__ void k_canon(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m, int32_t n,
+                        int b, uint64_t sent, uint64_t* __restrict__ keys, BuildCounters* cnt) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i - lane < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        bool in = i < m;
+        int32_t a = in ? src[i] : 0, c = in ? dst[i] : 0;
+        bool bad = in && (a < 0 || a >= n || c < 0 || c >= n);
+        bool loop = in && !bad && a == c;
+        if (in) {
+            uint64_t lo = (uint64_t)(uint32_t)(a < c ? a : c), hi = (uint64_t)(uint32_t)(a < c ? c : a);
+            keys[i] = (bad || loop) ? sent : ((lo << b) | hi);
+        }
+        if (bad) atomicMin(&cnt->bad_index, (long long)i);
+        unsigned lb = __ballot_sync(kFull, loop);
+        if (lane == 0 && lb) atomicAdd(&cnt->self_loops, (unsigned long long)__popc(lb));
+    }
+}
+
+struct UniquePred {
+    const uint64_t* k;
+    uint64_t sent;
+    __device__ bool operator()(int64_t i) const { return k[i] != sent && (i == 0 || k[i] != k[i - 1]); }
+};
+struct KeyVal {
+    const uint64_t* k;
+    __device__ uint64_t operator()(int64_t i) const { return k[i]; }
+};
+
+// --------------------------------------------------------------------------- a3: degrees
+__global__ void k_degree(const uint64_t* __restrict__ ukeys, int64_t mh, int b, int32_t* __restrict__ deg) {
+    const uint64_t mask = (1ull << b) - 1;
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i - lane < mh;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        bool in = i < mh;
+        uint64_t k = in ? ukeys[i] : 0;
+        uint32_t a = in ? (uint32_t)(k >> b) : 0xFFFFFFFFu;
+        // keys are sorted by their smaller endpoint: aggregate equal ones within the warp
+        unsigned peers = __match_any_sync(kFull, a);
+        if (in && lane == __ffs(peers) - 1) atomicAdd(&deg[a], __popc(peers));
+        if (in) atomicAdd(&deg[(uint32_t)(k & mask)], 1);
+    }
+}
+
+// --------------------------------------------------------------------------- a4: orientation
+__global__ void k_orient(const uint64_t* __restrict__ ukeys, int64_t mh, int b, const int32_t* __restrict__ deg,
+                         uint64_t* __restrict__ okeys) {
+    const uint64_t mask = (1ull << b) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mh; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = ukeys[i];
+        uint32_t a = (uint32_t)(k >> b), c = (uint32_t)(k & mask);  // a < c
+        int32_t da = deg[a], dc = deg[c];
+        bool a_first = da < dc || (da == dc);  // equal degrees: the smaller id a comes first
+        okeys[i] = a_first ? k : (((uint64_t)c << b) | a);
+    }
+}
+
+// --------------------------------------------------------------------------- a5: N+ lists
+__global__ void k_dhat_count(const uint64_t* __restrict__ okeys, int64_t mh, int b, int32_t* __restrict__ dhat) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i - lane < mh;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        bool in = i < mh;
+        uint32_t v = in ? (uint32_t)(okeys[i] >> b) : 0xFFFFFFFFu;
+        unsigned peers = __match_any_sync(kFull, v);
+        if (in && lane == __ffs(peers) - 1) atomicAdd(&dhat[v], __popc(peers));
+    }
+}
+
+struct DhatVal {
+    const int32_t* d;
+    __device__ uint64_t operator()(int64_t i) const { return (uint64_t)d[i]; }
+};
+
+__global__ void k_cols(const uint64_t* __restrict__ okeys, int64_t mh, int b, int32_t* __restrict__ cols) {
+    const uint64_t mask = (1ull << b) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mh; i += (int64_t)gridDim.x * blockDim.x)
+        cols[i] = (int32_t)(okeys[i] & mask);
+}
+
+__global__ void k_max_deg(const int32_t* __restrict__ deg, const int32_t* __restrict__ dhat, int32_t n,
+                          BuildCounters* cnt) {
+    int md = 0, mh = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        md = max(md, deg[i]);
+        mh = max(mh, dhat[i]);
+    }
+    md = warp_max(md);
+    mh = warp_max(mh);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&cnt->max_degree, md);
+        atomicMax(&cnt->max_dhat, mh);
+    }
+}
+
+// --------------------------------------------------------------------------- tasks
+__global__ void k_task_keys(const uint64_t* __restrict__ okeys, const int32_t* __restrict__ cols, int64_t mh, int b,
+                            const int32_t* __restrict__ dhat, uint64_t sent, uint64_t* __restrict__ tkeys,
+                            BuildCounters* cnt) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long sv = 0, su = 0, ss = 0, nt = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mh; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t v = (uint32_t)(okeys[i] >> b);
+        uint32_t u = (uint32_t)cols[i];
+        int32_t dv = dhat[v], du = dhat[u];
+        uint32_t o = dv >= du ? v : u, p = dv >= du ? u : v;
+        int32_t dp = dv >= du ? du : dv;
+        sv += (unsigned long long)dv;
+        su += (unsigned long long)du;
+        if (dp > 0) {
+            ss += (unsigned long long)dp;
+            nt += 1;
+            tkeys[i] = ((uint64_t)o << b) | p;
+        } else {
+            tkeys[i] = sent;
+        }
+    }
+    sv = warp_sum(sv);
+    su = warp_sum(su);
+    ss = warp_sum(ss);
+    nt = warp_sum(nt);
+    if (lane == 0) {
+        if (sv) atomicAdd(&cnt->sum_dhat_v, sv);
+        if (su) atomicAdd(&cnt->sum_dhat_u, su);
+        if (ss) atomicAdd(&cnt->sum_stream, ss);
+        if (nt) atomicAdd(&cnt->tasks, nt);
+    }
+}
+
+__global__ void k_task_records(const uint64_t* __restrict__ tkeys, int64_t T, int b, const int64_t* __restrict__ off,
+                               TaskRec* __restrict__ rec) {
+    const uint64_t mask = (1ull << b) - 1;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = tkeys[t];
+        uint32_t o = (uint32_t)(k >> b), p = (uint32_t)(k & mask);
+        int64_t s = off[p], e = off[p + 1];
+        TaskRec r;
+        r.owner = o;
+        r.partner = p;
+        r.pstart = (uint32_t)s;
+        r.plen = (uint32_t)(e - s);
+        rec[t] = r;
+    }
+}
+
+// --------------------------------------------------------------------------- driver
+
+static int bits_for(int32_t n) {
+    uint32_t maxid = n > 1 ? (uint32_t)(n - 1) : 1u;
+    int b = 32 - __builtin_clz(maxid);
+    return b < 1 ? 1 : b;
+}
+
+static unsigned grid_stride_blocks(int64_t n) {
+    int64_t want = ceil_div(n > 0 ? n : 1, kThreads);
+    int64_t cap = (int64_t)num_sms() * 16;
+    return (unsigned)(want < cap ? want : cap);
+}
+
+tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t m, int32_t n, cudaStream_t s) {
+    Allocator* al = &g->al;
+    const int b = bits_for(n);
+    const int nbits = 2 * b;
+    const uint64_t sent = (nbits >= 64) ? ~0ull : ((1ull << nbits) - 1);
+    g->n = n;
+    g->id_bits = b;
+    g->m_in = m;
+
+    DevBuf<BuildCounters> cnt;
+    TC_TRY(cnt.alloc(al, 1, s));
+    {
+        BuildCounters init{};
+        init.bad_index = LLONG_MAX;
+        TC_CUDA_TRY(cudaMemcpyAsync(cnt.ptr, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    }
+    DevBuf<uint64_t> ka, kb;
+    TC_TRY(ka.alloc(al, m > 0 ? m : 1, s));
+    TC_TRY(kb.alloc(al, m > 0 ? m : 1, s));
+
+    // a1
+    if (m > 0) {
+        k_canon<<<grid_stride_blocks(m), kThreads, 0, s>>>(src, dst, m, n, b, sent, ka.ptr, cnt.ptr);
+        note_launch();
+    }
+    TC_CUDA_TRY(cudaGetLastError());
+    // a2
+    uint64_t* sorted = nullptr;
+    TC_TRY(radix_sort_u64(ka.ptr, kb.ptr, m, nbits, al, s, &sorted));
+    uint64_t* other = sorted == ka.ptr ? kb.ptr : ka.ptr;
+    uint64_t mh64 = 0;
+    TC_TRY(compact(UniquePred{sorted, sent}, KeyVal{sorted}, m, other, al, s, &mh64));
+    BuildCounters hc;
+    TC_CUDA_TRY(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    TC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hc.bad_index != LLONG_MAX) {
+        g->self_loops = (int64_t)hc.self_loops;
+        g->bad_index = (int64_t)hc.bad_index;
+        return TC_ERR_VERTEX_RANGE;
+    }
+    const int64_t mh = (int64_t)mh64;
+    g->m_hat = mh;
+    g->self_loops = (int64_t)hc.self_loops;
+    g->duplicates = m - g->self_loops - mh;
+    if (g->opt.input_policy == TC_INPUT_STRICT && (g->self_loops > 0 || g->duplicates > 0)) return TC_ERR_INVALID_ARG;
+    if (mh >= (int64_t)0xFFFFFFFFll) return TC_ERR_UNSUPPORTED;  // task records index lists with uint32
+    uint64_t* ukeys = other;   // mh distinct keys
+    uint64_t* spare = sorted;  // free buffer of m keys
+
+    // a3
+    DevBuf<int32_t> deg, dhat;
+    TC_TRY(deg.alloc(al, n > 0 ? n : 1, s));
+    TC_TRY(dhat.alloc(al, n > 0 ? n : 1, s));
+    TC_CUDA_TRY(cudaMemsetAsync(deg.ptr, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));
+    TC_CUDA_TRY(cudaMemsetAsync(dhat.ptr, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));
+    if (mh > 0) {
+        k_degree<<<grid_stride_blocks(mh), kThreads, 0, s>>>(ukeys, mh, b, deg.ptr);
+        note_launch();
+    }
+    // a4
+    if (mh > 0) {
+        k_orient<<<grid_stride_blocks(mh), kThreads, 0, s>>>(ukeys, mh, b, deg.ptr, spare);
+        note_launch();
+    }
+    TC_CUDA_TRY(cudaGetLastError());
+    uint64_t* osorted = nullptr;
+    TC_TRY(radix_sort_u64(spare, ukeys, mh, nbits, al, s, &osorted));
+    uint64_t* free_buf = osorted == spare ? ukeys : spare;
+    // a5
+    if (mh > 0) {
+        k_dhat_count<<<grid_stride_blocks(mh), kThreads, 0, s>>>(osorted, mh, b, dhat.ptr);
+        note_launch();
+    }
+    DevBuf<int64_t> off;
+    DevBuf<int32_t> cols;
+    TC_TRY(off.alloc(al, (size_t)n + 1, s));
+    TC_TRY(cols.alloc(al, mh > 0 ? mh : 1, s));
+    {
+        // offsets = exclusive scan of dhat (values < 2^63, so the uint64 scan is the int64 array)
+        DevBuf<uint64_t> scr;
+        TC_TRY(scr.alloc(al, scan_scratch_words(n), s));
+        TC_CUDA_TRY(scan_exclusive(DhatVal{dhat.ptr}, n, reinterpret_cast<uint64_t*>(off.ptr), scr.ptr, s));
+    }
+    if (mh > 0) {
+        k_cols<<<grid_stride_blocks(mh), kThreads, 0, s>>>(osorted, mh, b, cols.ptr);
+        note_launch();
+    }
+    if (n > 0) {
+        k_max_deg<<<grid_stride_blocks(n), kThreads, 0, s>>>(deg.ptr, dhat.ptr, n, cnt.ptr);
+        note_launch();
+    }
+    TC_CUDA_TRY(cudaGetLastError());
+
+    // tasks
+    if (mh > 0) {
+        k_task_keys<<<grid_stride_blocks(mh), kThreads, 0, s>>>(osorted, cols.ptr, mh, b, dhat.ptr, sent,
+                                                                             free_buf, cnt.ptr);
+        note_launch();
+    }
+    TC_CUDA_TRY(cudaGetLastError());
+    uint64_t* tsorted = nullptr;
+    TC_TRY(radix_sort_u64(free_buf, osorted, mh, nbits, al, s, &tsorted));
+    TC_CUDA_TRY(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    TC_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t T = (int64_t)hc.tasks;
+    DevBuf<TaskRec> rec;
+    TC_TRY(rec.alloc(al, T > 0 ? T : 1, s));
+    if (T > 0) {
+        k_task_records<<<grid_stride_blocks(T), kThreads, 0, s>>>(tsorted, T, b, off.ptr, rec.ptr);
+        note_launch();
+    }
+    TC_CUDA_TRY(cudaGetLastError());
+
+    g->tasks = T;
+    g->max_degree = hc.max_degree;
+    g->max_dhat = hc.max_dhat;
+    g->sum_dhat_v = hc.sum_dhat_v;
+    g->sum_dhat_u = hc.sum_dhat_u;
+    g->sum_stream = hc.sum_stream;
+    // hand the arrays to the handle; the key buffers and counters are released here
+    g->deg = deg.detach();
+    g->off = off.detach();
+    g->cols = cols.detach();
+    g->trec = rec.detach();
+    g->bytes = (int64_t)align_up((size_t)(n > 0 ? n : 1) * 4, 256) + (int64_t)align_up(((size_t)n + 1) * 8, 256) +
+               (int64_t)align_up((size_t)(mh > 0 ? mh : 1) * 4, 256) +
+               (int64_t)align_up((size_t)(T > 0 ? T : 1) * sizeof(TaskRec), 256);
+    TC_CUDA_TRY(cudaStreamSynchronize(s));
+    return TC_OK;
+}
+
+}  // namespace tcg

@@ -1,0 +1,95 @@
+// graph.cuh -- the device representation behind a tc_graph_t handle.
+#pragma once
+
+#include "common.cuh"
+
+namespace tcg {
+
+// One task = one oriented edge, owned by the endpoint with the longer N+ list.  The owner's
+// list is staged in shared memory; the partner's list N+(partner) = cols[pstart, pstart+plen)
+// is streamed through it.  16 bytes, so a warp reads its tasks with one vector load each.
+struct __align__(16) TaskRec {
+    uint32_t owner;
+    uint32_t partner;
+    uint32_t pstart;
+    uint32_t plen;
+};
+
+// Device-side scheduling state of one count (Sec. V-B): total cost C, the initial share H
+// (Eq. 1), the Eq. 2 floor, and the head of the dynamic queue.
+struct Sched {
+    unsigned long long C;
+    unsigned long long H;
+    unsigned long long min_chunk;
+    unsigned long long head;
+    unsigned long long n_chunks;
+    unsigned long long total;
+};
+
+// Device counters written by the build kernels.
+struct BuildCounters {
+    unsigned long long self_loops;
+    unsigned long long unique;
+    unsigned long long tasks;
+    unsigned long long sum_dhat_v;
+    unsigned long long sum_dhat_u;
+    unsigned long long sum_stream;
+    long long bad_index;
+    int max_degree;
+    int max_dhat;
+};
+
+// Workspace of the count, allocated on the handle's first count and reused.
+struct CountWork {
+    uint64_t* prefix = nullptr;   // T + 1
+    int64_t prefix_len = 0;
+    uint64_t* scan_scr = nullptr;
+    int64_t scan_words = 0;
+    uint64_t* fcost = nullptr;    // n, per-vertex cost models only
+    Sched* sched = nullptr;
+    unsigned long long* result = nullptr;  // device copy of the last total
+};
+
+}  // namespace tcg
+
+struct tc_graph {
+    int device = 0;
+    tc_options opt{};
+    tcg::Allocator al;
+    int32_t n = 0;
+    int id_bits = 1;
+    int64_t m_in = 0, self_loops = 0, duplicates = 0, m_hat = 0, tasks = 0, bad_index = -1;
+    int32_t max_degree = 0, max_dhat = 0;
+    uint64_t sum_dhat_v = 0, sum_dhat_u = 0, sum_stream = 0;
+    // device arrays owned by the handle
+    int32_t* deg = nullptr;        // n
+    int64_t* off = nullptr;        // n + 1
+    int32_t* cols = nullptr;       // m_hat
+    tcg::TaskRec* trec = nullptr;  // tasks
+    tcg::DevStatus* status = nullptr;
+    tcg::CountWork work;
+    int64_t bytes = 0;             // device bytes held
+    cudaStream_t last_stream = nullptr;  // stream of the last call; tc_free waits for it
+};
+
+namespace tcg {
+
+// The count pipeline (count.cu): cost prefix, schedule init, persistent count kernel.
+// Results: total into *total_dev (device uint64), optional t_v (device, n) and per-edge
+// counts (device, m_hat), optional trace.  Enqueue only (no synchronisation).
+tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsigned long long* total_dev,
+                        unsigned long long* t_v, uint32_t* per_edge, tc_count_trace* trace);
+
+tc_status ensure_count_work(tc_graph* g, const tc_options& opt, cudaStream_t s);
+
+tc_status vertex_cost_enqueue(tc_graph* g, int fn, cudaStream_t s, uint64_t* f);
+
+tc_status clustering_enqueue(tc_graph* g, const uint64_t* t_v, double* cc, cudaStream_t s);
+
+// Build (build.cu).  src/dst are device pointers here.
+tc_status build_graph(tc_graph* g, const int32_t* src_d, const int32_t* dst_d, int64_t m, int32_t n,
+                      cudaStream_t s);
+
+tc_status check_options(const tc_options& o);
+
+}  // namespace tcg

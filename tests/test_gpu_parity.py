@@ -1,0 +1,296 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Integer results must match bit-exactly (tolerance 0): N+ lists and degrees (steps
+a1-a5), the task array and the schedule (a6), per-edge counts (a7), totals and
+T_v (a8).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from graphgen import families as F
+from graphgen import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # collected on CPU only under -m gpu
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_1406_5687_gb300 as tc  # noqa: E402
+
+
+def _graphs():
+    import graphgen
+    out = {
+        "empty_n0": (0, np.zeros(0, np.int32), np.zeros(0, np.int32)),
+        "no_edges": (17, np.zeros(0, np.int32), np.zeros(0, np.int32)),
+        "k3": F.complete(3),
+        "k60": F.complete(60),
+        "wheel_1000": F.wheel(1000),
+        "book_5000": F.book(5000),
+        "tripartite": F.complete_tripartite(3, 40, 70),
+        "star_matching": F.star_matching(3000),
+        "friendship": F.friendship(700),
+        "bipartite": F.complete_bipartite(30, 90),
+        "tree": F.random_tree(5000, 1),
+    }
+    n = 20000
+    s, d = graphgen.erdos_renyi(n, 150000, 21)
+    out["er_20k"] = (n, s, d)
+    n = 30000
+    s, d = graphgen.barabasi_albert(n, 12, 22)
+    out["ba_30k"] = (n, s, d)
+    n = 200000
+    s, d = graphgen.chung_lu(n, 2.1, 20.0, 8000.0, 2_000_000, 23)
+    out["cl_200k"] = (n, s, d)
+    n = 3000
+    s, d = graphgen.chung_lu(n, 2.05, 150.0, 2500.0, 400_000, 24)  # dense: lists longer than one piece
+    out["cl_dense"] = (n, s, d)
+    return out
+
+
+GRAPHS = _graphs()
+
+
+def oracle_csr(n, s, d):
+    return oracle.oriented_csr(oracle.simple_graph(n, s, d))
+
+
+@pytest.fixture(scope="module")
+def built():
+    res = {}
+    for name, (n, s, d) in GRAPHS.items():
+        res[name] = (tc.Graph.build(s, d, n), oracle_csr(n, s, d))
+    yield res
+    for g, _ in res.values():
+        g.free()
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_csr_matches_oracle(built, name):
+    g, csr = built[name]
+    deg, off, cols, tasks = g.csr()
+    assert np.array_equal(deg.cpu().numpy(), csr.deg)
+    assert np.array_equal(off.cpu().numpy(), csr.off)
+    assert np.array_equal(cols.cpu().numpy(), csr.cols)
+    info = g.info()
+    n, s, d = GRAPHS[name]
+    sg = oracle.simple_graph(n, s, d)
+    assert info["m_hat"] == sg.m_hat
+    assert info["self_loops"] == sg.self_loops
+    assert info["duplicates"] == sg.duplicates
+    assert info["max_degree"] == (int(csr.deg.max()) if n else 0)
+    assert info["max_dhat"] == (int(np.diff(csr.off).max()) if n else 0)
+    dh = np.diff(csr.off)
+    assert info["sum_dhat_v"] == int(np.repeat(dh, dh).sum())
+    assert info["sum_dhat_u"] == int(dh[csr.cols].sum())
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_tasks_match_oracle(built, name):
+    g, csr = built[name]
+    _, _, _, tasks = g.csr()
+    t = tasks.cpu().numpy().astype(np.int64)
+    o, p = oracle.tasks(csr)
+    assert np.array_equal(t[:, 0], o) and np.array_equal(t[:, 1], p)
+    assert np.array_equal(t[:, 2], csr.off[p]) and np.array_equal(t[:, 3], np.diff(csr.off)[p])
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_count_matches_oracle(built, name):
+    g, csr = built[name]
+    assert g.count() == oracle.count(csr)
+
+
+@pytest.mark.parametrize("name", ["k60", "wheel_1000", "book_5000", "er_20k", "ba_30k", "cl_200k", "cl_dense"])
+def test_per_vertex_and_per_edge(built, name):
+    g, csr = built[name]
+    T, pe, tv = oracle.count(csr, per_edge=True, per_vertex=True)
+    T1, tv_g = g.count_per_vertex()
+    assert T1 == T
+    assert np.array_equal(tv_g.cpu().numpy().astype(np.uint64), tv)
+    T2, pe_g = g.count_per_edge()
+    assert T2 == T
+    assert np.array_equal(pe_g.cpu().numpy().astype(np.uint32), pe)
+    cc = g.clustering(tv_g).cpu().numpy()
+    degf = csr.deg.astype(np.float64)
+    want = np.where(csr.deg >= 2, 2.0 * tv.astype(np.float64) / np.maximum(degf * (degf - 1.0), 1.0), 0.0)
+    assert np.array_equal(cc, want)
+
+
+@pytest.mark.parametrize("name", ["wheel_1000", "er_20k", "cl_200k", "cl_dense"])
+@pytest.mark.parametrize("fn", [tc.TC_FN_ONE, tc.TC_FN_DEGREE, tc.TC_FN_PATRIC, tc.TC_FN_NEW])
+def test_vertex_cost(built, name, fn):
+    g, csr = built[name]
+    f = g.vertex_cost(fn).cpu().numpy().astype(np.uint64)
+    assert np.array_equal(f, oracle.vertex_cost(csr, fn))
+
+
+@pytest.mark.parametrize("name", ["er_20k", "cl_200k", "cl_dense", "book_5000"])
+@pytest.mark.parametrize("model,piece", [(tc.TC_COST_EDGE, 1024), (tc.TC_COST_EDGE, 128), (tc.TC_COST_MERGE, 512),
+                                         (tc.TC_COST_DEGREE, 256), (tc.TC_COST_PATRIC, 1024),
+                                         (tc.TC_COST_NEW, 2048), (tc.TC_COST_ONE, 1024)])
+def test_schedule_matches_oracle(built, name, model, piece):
+    """The chunks the workers took are exactly Eq. 1 + Eq. 2 over the oracle's task costs."""
+    g, csr = built[name]
+    wpb = 16 if piece <= 1024 else 4
+    opt = tc.default_options(cost_model=model, piece=piece, warps_per_block=wpb)
+    T, meta, chunks, busy = g.count_ex(opt, trace_cap=1 << 20, busy=True)
+    assert T == oracle.count(csr)
+    o, p = oracle.tasks(csr)
+    if model == tc.TC_COST_EDGE:
+        cost = oracle.task_costs(csr, o, p, oracle.MODEL_EDGE, piece=piece, c_task=4, c_owner=32)
+    elif model == tc.TC_COST_MERGE:
+        cost = oracle.task_costs(csr, o, p, oracle.MODEL_MERGE)
+    else:
+        cost = oracle.task_costs(csr, o, p, oracle.MODEL_VERTEX, fn=model - tc.TC_COST_ONE)
+    assert meta["total_cost"] == int(cost.sum())
+    cb, tb = oracle.schedule(cost, meta["n_workers"], meta["min_chunk"])
+    want = np.stack([cb[:-1], cb[1:], tb[:-1], tb[1:]], axis=1).astype(np.int64)
+    got = chunks.cpu().numpy()
+    assert meta["n_chunks"] == len(want)
+    W = meta["n_workers"]
+    # static chunks are recorded by worker; dynamic ones in pop order -- compare as sets ordered by cost
+    got = got[np.lexsort((got[:, 1], got[:, 0]))]
+    want = want[np.lexsort((want[:, 1], want[:, 0]))]
+    assert np.array_equal(got, want)
+    b = busy.cpu().numpy()
+    assert b.shape[0] == W and int(b[:, 1].sum()) == len(want)
+
+
+@pytest.mark.parametrize("static_percent", [0, 25, 50, 100])
+@pytest.mark.parametrize("min_chunk", [0, 1, 100000])
+def test_schedule_parameters_keep_the_count(built, static_percent, min_chunk):
+    g, csr = built["cl_200k"]
+    opt = tc.default_options(static_percent=static_percent, min_chunk=min_chunk)
+    T, *_ = g.count_ex(opt)
+    assert T == oracle.count(csr)
+
+
+@pytest.mark.parametrize("wpb,piece,bps", [(1, 128, 0), (4, 512, 2), (16, 1024, 1), (4, 2048, 0), (8, 256, 3)])
+def test_launch_shapes_keep_the_count(built, wpb, piece, bps):
+    g, csr = built["cl_dense"]
+    opt = tc.default_options(warps_per_block=wpb, piece=piece, blocks_per_sm=bps)
+    T, *_ = g.count_ex(opt)
+    assert T == oracle.count(csr)
+
+
+def test_device_input_and_dirty_input():
+    n, s, d = GRAPHS["cl_200k"]
+    rng = np.random.default_rng(5)
+    pick = rng.integers(0, len(s), 5000)
+    s2 = np.concatenate([s, d[pick], np.arange(100, dtype=np.int32)])
+    d2 = np.concatenate([d, s[pick], np.arange(100, dtype=np.int32)])
+    order = rng.permutation(len(s2))
+    s2, d2 = s2[order], d2[order]
+    sg = oracle.simple_graph(n, s2, d2)
+    T = oracle.count(oracle.oriented_csr(sg))
+    with tc.Graph.build(torch.from_numpy(s2).cuda(), torch.from_numpy(d2).cuda(), n) as g:
+        info = g.info()
+        assert (info["m_hat"], info["self_loops"], info["duplicates"]) == (sg.m_hat, sg.self_loops, sg.duplicates)
+        assert g.count() == T
+
+
+def test_input_errors():
+    with pytest.raises(tc.TcError) as e:
+        tc.Graph.build(np.array([0, 5], np.int32), np.array([1, 2], np.int32), 5)
+    assert e.value.code == tc._lib.TC_ERR_VERTEX_RANGE
+    with pytest.raises(tc.TcError) as e:
+        tc.Graph.build(np.array([0, -3], np.int32), np.array([1, 2], np.int32), 5)
+    assert e.value.code == tc._lib.TC_ERR_VERTEX_RANGE
+    strict = tc.default_options(input_policy=tc.TC_INPUT_STRICT)
+    with pytest.raises(tc.TcError) as e:
+        tc.Graph.build(np.array([0, 1], np.int32), np.array([1, 0], np.int32), 5, strict)
+    assert e.value.code == tc._lib.TC_ERR_INVALID_ARG
+    with pytest.raises(tc.TcError) as e:
+        tc.Graph.build(np.array([2], np.int32), np.array([2], np.int32), 5, strict)
+    assert e.value.code == tc._lib.TC_ERR_INVALID_ARG
+    with tc.Graph.build(np.array([0, 1, 2], np.int32), np.array([1, 2, 0], np.int32), 3, strict) as g:
+        assert g.count() == 1
+
+
+def test_budget_and_allocator_failure():
+    n, s, d = GRAPHS["er_20k"]
+    small = tc.default_options(hbm_budget_bytes=1 << 16)
+    with pytest.raises(tc.TcError) as e:
+        tc.Graph.build(s, d, n, small)
+    assert e.value.code == tc._lib.TC_ERR_BUDGET
+
+    calls = {"n": 0}
+
+    @tc._lib.ALLOC_FN
+    def failing_alloc(ctx, nbytes, stream):
+        calls["n"] += 1
+        return None
+
+    @tc._lib.RELEASE_FN
+    def release(ctx, p, stream):
+        pass
+
+    opt = tc.default_options(alloc=failing_alloc, release=release)
+    with pytest.raises(tc.TcError) as e:
+        tc.Graph.build(s, d, n, opt)
+    assert e.value.code == tc._lib.TC_ERR_OOM and calls["n"] >= 1
+
+
+def test_caller_allocator_is_used():
+    """Device memory can come from torch's caching allocator through the hooks."""
+    n, s, d = GRAPHS["ba_30k"]
+    live = {}
+
+    @tc._lib.ALLOC_FN
+    def alloc(ctx, nbytes, stream):
+        t = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    @tc._lib.RELEASE_FN
+    def release(ctx, p, stream):
+        live.pop(p, None)
+
+    opt = tc.default_options(alloc=alloc, release=release)
+    g = tc.Graph.build(s, d, n, opt)
+    assert len(live) > 0
+    assert g.count() == oracle.count(oracle_csr(n, s, d))
+    g.free()
+    assert len(live) == 0
+
+
+def test_async_count_and_graph_capture(built):
+    g, csr = built["cl_200k"]
+    T = oracle.count(csr)
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    g.count_async(out)
+    g.check()
+    assert int(out.item()) == T
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        g.count_async(out)  # warm-up on the capture stream: the workspace already exists
+    s.synchronize()
+    cg = torch.cuda.CUDAGraph()
+    out2 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with torch.cuda.graph(cg, stream=s):
+        g.count_async(out2, stream=s)
+    for _ in range(3):
+        out2.zero_()
+        cg.replay()
+        torch.cuda.synchronize()
+        assert int(out2.item()) == T
+
+
+def test_er_golden():
+    """The ER workload's stored oracle values (tests/golden/er_10k.txt)."""
+    import os
+    gold = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "er_10k.txt")) as f:
+        for line in f:
+            if not line.startswith("#"):
+                k, v = line.split()
+                gold[k] = v
+    s, d = W.ER_10K.edges()
+    with tc.Graph.build(s, d, W.ER_10K.n) as g:
+        assert g.info()["m_hat"] == int(gold["m_hat"])
+        assert g.count() == int(gold["triangles"])
+        T, tv = g.count_per_vertex()
+        assert int(tv.sum().item()) == int(gold["sum_t_v"])
