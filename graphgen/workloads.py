@@ -66,7 +66,11 @@ ER_10K = GraphSpec("er", n=10_000, m=100_000, seed=0)
 BA_1M = GraphSpec("ba", n=1_000_000, k=50, seed=1)
 CL_10M = GraphSpec("cl", n=10_000_000, gamma=2.1, avg_deg=40.0, w_max=1e5, draws=200_000_000, seed=2)
 
-SINGLE = {"er": ER_10K, "ba": BA_1M, "cl": CL_10M}
+# the Chung-Lu recipe at one fifth of the vertices and edges (w_0 scaled by sqrt(n)), for
+# profiling captures that must hold only a few GB on the device
+CL_2M = GraphSpec("cl", n=2_000_000, gamma=2.1, avg_deg=40.0, w_max=44721.0, draws=40_000_000, seed=2)
+
+SINGLE = {"er": ER_10K, "ba": BA_1M, "cl": CL_10M, "cl_small": CL_2M}
 
 
 def _unit(seed: int, tag: int, i: int) -> float:

@@ -37,7 +37,7 @@ class _CudaArray:
     """Zero-copy view of library-owned device memory for torch.as_tensor."""
 
     def __init__(self, ptr: int, n: int, typestr: str):
-        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
                                          "version": 3, "strides": None}
 
 

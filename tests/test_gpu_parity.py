@@ -152,8 +152,8 @@ def test_schedule_matches_oracle(built, name, model, piece):
     assert meta["n_chunks"] == len(want)
     W = meta["n_workers"]
     # static chunks are recorded by worker; dynamic ones in pop order -- compare as sets ordered by cost
-    got = got[np.lexsort((got[:, 1], got[:, 0]))]
-    want = want[np.lexsort((want[:, 1], want[:, 0]))]
+    got = got[np.lexsort((got[:, 3], got[:, 2], got[:, 1], got[:, 0]))]
+    want = want[np.lexsort((want[:, 3], want[:, 2], want[:, 1], want[:, 0]))]
     assert np.array_equal(got, want)
     b = busy.cpu().numpy()
     assert b.shape[0] == W and int(b[:, 1].sum()) == len(want)
