@@ -150,8 +150,8 @@ def stored_traffic(workload):
     return rec.get("dram_bytes_per_launch")
 
 
-def algorithmic_bytes(g, piece):
-    """Bytes the count kernel must move per launch if nothing were cached:
+def algorithmic_bytes(g, piece, small_max):
+    """Bytes the count kernels must move per count if nothing were cached:
     every task reads its 16-byte record and streams its partner list once per piece of
     its owner's list (4 B per entry); every owner stages its own list once (4 B per entry)
     and reads its two offsets (16 B).  Also returns the merge-model figure
@@ -163,7 +163,7 @@ def algorithmic_bytes(g, piece):
     dh = np.diff(off)
     owner = t[:, 0].astype(np.int64)
     plen = t[:, 3].astype(np.int64)
-    pieces = (dh[owner] + piece - 1) // piece
+    pieces = np.where(dh[owner] <= small_max, 1, (dh[owner] + piece - 1) // piece)
     streamed = int((pieces * plen).sum()) * 4
     owners = np.unique(owner)
     staged = int(dh[owners].sum()) * 4
@@ -261,7 +261,7 @@ def run_gpu(args, rank, world, local):
     g = tc.Graph.build(s_dev, d_dev, spec.n, opt)
     info = g.info()
     T_ref = g.count()
-    b_alg, b_merge, work = algorithmic_bytes(g, opt.piece)
+    b_alg, b_merge, work = algorithmic_bytes(g, opt.piece, opt.small_max)
     g.free()
     m_hat = info["m_hat"]
 
@@ -276,7 +276,8 @@ def run_gpu(args, rank, world, local):
         gg.free()
         if T != T_ref:
             raise RuntimeError(f"count changed between steps: {T} != {T_ref}")
-        return e0.elapsed_time(e2), e0.elapsed_time(e1), e1.elapsed_time(e2), meta["kernel_ms"], meta["prefix_ms"]
+        return (e0.elapsed_time(e2), e0.elapsed_time(e1), e1.elapsed_time(e2), meta["kernel_ms"], meta["prefix_ms"],
+                meta["kernel_small_ms"], meta["kernel_big_ms"])
 
     for _ in range(args.warmup):
         device_step()
@@ -306,6 +307,8 @@ def run_gpu(args, rank, world, local):
     count_ms = statistics.mean(x[2] for x in steps)
     kernel_ms = statistics.mean(x[3] for x in steps)
     prefix_ms = statistics.mean(x[4] for x in steps)
+    small_ms = statistics.mean(x[5] for x in steps)
+    big_ms = statistics.mean(x[6] for x in steps)
 
     # e2e: edge list in pinned host memory, copies and the 8-byte result read inside the step
     e2e = None
@@ -333,7 +336,7 @@ def run_gpu(args, rank, world, local):
 
     peak, peak_kind = measured_peaks()
     achieved = b_alg / (kernel_ms / 1e3) / 1e9
-    roofline = {"kernel": "k_count (persistent intersection, steps a7-a8)", "bound": "hbm",
+    roofline = {"kernel": "k_count_small + k_count_big (persistent intersection, steps a7-a8)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"hbm_gbs of {peak_kind}", "traffic": stored_traffic(args.workload),
                 "algorithmic_bytes": b_alg, "launch_ms": kernel_ms,
@@ -353,9 +356,10 @@ def run_gpu(args, rank, world, local):
                            "l2": "inputs larger than L2 (edge list, lists and tasks each exceed 129 MB)",
                            "parallelism": "replicas" if world > 1 else "single",
                            "options": {"piece": opt.piece, "warps_per_block": opt.warps_per_block,
+                                       "big_warps": opt.big_warps, "small_max": opt.small_max,
                                        "cost_model": "edge", "static_percent": opt.static_percent}},
                 "phases_ms": {"build": build_ms, "count": count_ms, "count_prefix": prefix_ms,
-                              "count_kernel": kernel_ms},
+                              "count_kernels": kernel_ms, "count_kernel_small": small_ms, "count_kernel_big": big_ms},
                 "count_only": {"value": m_hat / (count_ms / 1e3), "unit": UNIT,
                                "note": "m_hat / (cost prefix + schedule + intersection), lists resident"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -92,16 +92,27 @@ typedef enum tc_input_policy { TC_INPUT_SANITIZE = 0, TC_INPUT_STRICT = 1 } tc_i
 typedef void* (*tc_alloc_fn)(void* ctx, size_t bytes, tc_stream_t stream);
 typedef void (*tc_release_fn)(void* ctx, void* ptr, tc_stream_t stream);
 
+/*
+ * Tasks fall in two classes by the length of the owner's list.  Small owners (at most
+ * small_max entries) are counted by one warp each, with a per-warp hash table;
+ * big owners by a whole block, whose warps share one table of 8 * piece slots
+ * (lists longer than `piece` are staged in pieces, each partner list streamed once
+ * per piece).
+ */
 typedef struct tc_options {
     int32_t input_policy;      /* tc_input_policy */
     int32_t cost_model;        /* tc_cost_model */
-    int32_t piece;             /* owner-list entries staged per shared-memory hash table: 256, 512 or 1024 (default 1024) */
-    int32_t warps_per_block;   /* workers per block of the count kernel: 4, 8 or 16 (default 8) */
-    int32_t blocks_per_sm;     /* resident blocks per SM of the count kernel (0 = as many as fit) */
+    int32_t piece;             /* big owners: list entries staged per block table: 256..4096, power of 2 (default 2048) */
+    int32_t warps_per_block;   /* small-class kernel: warps (workers) per block: 1..16, power of 2 (default 8) */
+    int32_t blocks_per_sm;     /* cap on resident blocks per SM of both count kernels (0 = as many as fit) */
+    int32_t big_warps;         /* big-class kernel: warps per block (one worker): 4, 8 or 16 (default 16) */
+    int32_t small_max;         /* build option: owners with at most this many list entries are small:
+                                  0, 16, 32, 64, 128 or 256 (default 64) */
     int32_t static_percent;    /* share of the total cost handed out as initial tasks (Eq. 1); default 50 */
     int64_t min_chunk;         /* floor of an Eq. 2 chunk, in cost units (0 = automatic) */
     int32_t c_task;            /* TC_COST_EDGE per-task constant (default 4) */
     int32_t c_owner;           /* TC_COST_EDGE per-owner constant (default 32) */
+    int32_t reserved;
     int64_t hbm_budget_bytes;  /* device memory a build may hold at its peak (0 = no limit) */
     int64_t retry_limit;       /* bound on any device retry loop before TC_ERR_TIMEOUT (0 = default 1<<24) */
     tc_alloc_fn alloc;         /* optional allocator hooks (both or neither) */
@@ -190,6 +201,7 @@ typedef struct tc_graph_info {
     int64_t duplicates;    /* merged repeats, either orientation (sanitize) */
     int64_t m_hat;         /* distinct undirected edges = oriented edges */
     int64_t tasks;         /* oriented edges whose partner list is non-empty */
+    int64_t tasks_small;   /* of which owned by small owners (they come first in the task array) */
     uint64_t sum_dhat_v;   /* sum over oriented edges (v,u) of d^_v */
     uint64_t sum_dhat_u;   /* sum over oriented edges (v,u) of d^_u */
     uint64_t sum_stream;   /* sum over tasks of d^_partner: list entries the count kernel streams (piece 1024) */
@@ -203,8 +215,9 @@ tc_status tc_graph_get_info(tc_graph_t g, tc_graph_info* info);
  *   deg   n int32          d_v
  *   off   n+1 int64        N+(v) = cols[off[v] .. off[v+1])
  *   cols  m_hat int32      ascending within each list
- *   tasks 4*tasks uint32   one record per task, sorted by (owner, partner):
- *                          owner, partner, start of N+(partner) in cols, |N+(partner)|
+ *   tasks 4*tasks uint32   one record per task, sorted by (class, owner, partner), the
+ *                          small class first: owner, partner, start of N+(partner) in
+ *                          cols, |N+(partner)|
  * Any output pointer may be NULL.
  */
 tc_status tc_graph_csr(tc_graph_t g, const int32_t** deg, const int64_t** off, const int32_t** cols,
@@ -217,19 +230,24 @@ tc_status tc_graph_csr(tc_graph_t g, const int32_t** deg, const int64_t** off, c
 tc_status tc_vertex_cost(tc_graph_t g, int32_t fn, tc_stream_t stream, uint64_t* f);
 
 /*
- * Count with explicit options and a record of the schedule (steps a6-a8).
- *   opt      NULL = the handle's options; only the count fields are used.
+ * Count with explicit options and a record of the schedule (steps a6-a8).  Each task
+ * class is scheduled on its own (Eq. 1 + Eq. 2 over its own costs, class c in cost
+ * units counted from 0) by its own kernel.
+ *   opt      NULL = the handle's options; the build-time small_max is always the handle's.
  *   total    host; receives T.
  *   trace    NULL, or a record the count fills in:
  *              chunks  device, 4*cap uint64 or NULL: one record per chunk a worker
- *                      took, (cost_lo, cost_hi, task_lo, task_hi), in no
- *                      particular order; records beyond cap are dropped;
- *              workers_busy device, 2*W uint64 or NULL: per worker, (clock64
- *                      cycles spent on tasks, chunks taken) -- the per-worker
- *                      idle time of Sec. V-E;
- *            and on return: n_chunks (records produced), n_workers (W),
- *            total_cost (C), min_chunk (the Eq. 2 floor used), prefix_ms and
- *            kernel_ms (CUDA events recorded on `stream` around the two phases).
+ *                      took, ((class << 56) | cost_lo, cost_hi, task_lo, task_hi),
+ *                      task indices into the whole task array, in no particular
+ *                      order; records beyond cap are dropped;
+ *              workers_busy device, 2*(n_workers[0] + n_workers[1]) uint64 or
+ *                      NULL: per worker (small-class warps first, then big-class
+ *                      blocks), (clock64 cycles spent on tasks, chunks taken) --
+ *                      the per-worker idle time of Sec. V-E;
+ *            and on return: n_chunks (records produced), and per class c:
+ *            n_workers[c] (W), total_cost[c] (C), min_chunk[c] (the Eq. 2 floor
+ *            used); tasks_small; the CUDA-event times of the cost prefix and
+ *            schedule set-up (prefix_ms) and of each class's kernel.
  * With trace != NULL the call synchronises `stream` before returning.
  */
 typedef struct tc_count_trace {
@@ -237,11 +255,14 @@ typedef struct tc_count_trace {
     int64_t cap;
     uint64_t* workers_busy;
     int64_t n_chunks;
-    int64_t n_workers;
-    uint64_t total_cost;
-    uint64_t min_chunk;
-    float prefix_ms;   /* out: CUDA-event time of the cost prefix and schedule set-up (a6) */
-    float kernel_ms;   /* out: CUDA-event time of the persistent intersection kernel (a7-a8) */
+    int64_t n_workers[2];
+    uint64_t total_cost[2];
+    uint64_t min_chunk[2];
+    int64_t tasks_small;
+    float prefix_ms;        /* a6: task costs, prefix, schedule set-up */
+    float kernel_small_ms;  /* a7-a8, small-owner kernel */
+    float kernel_big_ms;    /* a7-a8, big-owner kernel */
+    float reserved;
 } tc_count_trace;
 
 tc_status tc_count_ex(tc_graph_t g, const tc_options* opt, tc_stream_t stream, uint64_t* total,

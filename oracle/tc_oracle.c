@@ -32,7 +32,8 @@
  *                     (Sec. IV-F), dh = effective degree |N_v|.
  *   or_tasks,         The GPU's work decomposition, restated from its
  *   or_task_costs,    definition: each oriented edge becomes one task owned by
- *   or_schedule       the endpoint with the longer list; task costs; the chunk
+ *   or_schedule       the endpoint with the longer list, in a small or a big
+ *                     class by the owner's list length; task costs; the chunk
  *                     table of the dynamic load balancing scheme -- the first
  *                     half of the total cost split into W equal initial tasks
  *                     (Sec. V-B, Eq. 1) and the rest handed out in chunks of
@@ -246,14 +247,17 @@ int or_vertex_cost(int fn, int32_t n, const int32_t* deg, const int64_t* off, co
  * (v, u) the owner is the endpoint with the longer list (v when dh_v >= dh_u) and
  * the partner is the other one; the triangle count of the edge is
  * |N_owner intersect N_partner|.  Tasks whose partner list is empty are dropped
- * (they count nothing).  Tasks are sorted by (owner, partner).
- * owner/partner need capacity m_hat.  Returns the number of tasks, or -1 on OOM.
+ * (they count nothing).  A task is "small" when its owner's list has at most
+ * small_max entries, else "big".  Tasks are sorted by (class, owner, partner):
+ * all small tasks first.  owner/partner need capacity m_hat; *n_small receives the
+ * number of small tasks.  Returns the number of tasks, or -1 on OOM.
  */
-int64_t or_tasks(int32_t n, const int64_t* off, const int32_t* cols, int32_t* owner, int32_t* partner) {
+int64_t or_tasks(int32_t n, const int64_t* off, const int32_t* cols, int64_t small_max, int32_t* owner,
+                 int32_t* partner, int64_t* n_small) {
     int64_t mh = off[n];
     uint64_t* key = (uint64_t*)malloc((size_t)(mh > 0 ? mh : 1) * sizeof(uint64_t));
     if (!key) return -1;
-    int64_t t = 0;
+    int64_t t = 0, ns = 0;
     for (int32_t v = 0; v < n; ++v) {
         int64_t dv = off[v + 1] - off[v];
         for (int64_t i = off[v]; i < off[v + 1]; ++i) {
@@ -262,15 +266,18 @@ int64_t or_tasks(int32_t n, const int64_t* off, const int32_t* cols, int32_t* ow
             int32_t o = dv >= du ? v : u;
             int32_t p = dv >= du ? u : v;
             if (off[p + 1] - off[p] == 0) continue;
-            key[t++] = ((uint64_t)(uint32_t)o << 32) | (uint32_t)p;
+            uint64_t big = (off[o + 1] - off[o]) > small_max ? 1u : 0u;
+            if (!big) ++ns;
+            key[t++] = (big << 63) | ((uint64_t)(uint32_t)o << 31) | (uint32_t)p;
         }
     }
     qsort(key, (size_t)t, sizeof(uint64_t), cmp_u64);
     for (int64_t i = 0; i < t; ++i) {
-        owner[i] = (int32_t)(key[i] >> 32);
-        partner[i] = (int32_t)(key[i] & 0xFFFFFFFFu);
+        owner[i] = (int32_t)((key[i] >> 31) & 0xFFFFFFFFu);
+        partner[i] = (int32_t)(key[i] & 0x7FFFFFFFu);
     }
     free(key);
+    *n_small = ns;
     return t;
 }
 
@@ -279,15 +286,16 @@ enum { OR_MODEL_EDGE = 0, OR_MODEL_MERGE = 1, OR_MODEL_VERTEX = 2 };
 /*
  * Cost of each task.
  *   EDGE   (the GPU's own model of its hash-probe work): the owner's list is
- *          staged in pieces of at most `piece` entries, each partner list is
- *          streamed once per piece: cost = pieces(owner) * (dh_partner + c_task);
- *          the owner's last task also carries the staging cost dh_owner + c_owner.
+ *          staged in pieces of at most `piece` entries (one piece when it has at
+ *          most small_max entries), each partner list is streamed once per piece:
+ *          cost = pieces(owner) * (dh_partner + c_task); the owner's last task also
+ *          carries the staging cost dh_owner + c_owner.
  *   MERGE  the paper's per-edge merge cost dh_v + dh_u (Sec. III-A).
  *   VERTEX the paper's per-vertex cost f (from or_vertex_cost with function fn),
  *          put on the owner's last task so that a chunk never splits an owner:
  *          the atomic task <v,1> of Sec. V-A.
  */
-int or_task_costs(int model, int fn, int32_t piece, int32_t c_task, int32_t c_owner,
+int or_task_costs(int model, int fn, int32_t piece, int64_t small_max, int32_t c_task, int32_t c_owner,
                   int32_t n, const int32_t* deg, const int64_t* off, const int32_t* cols,
                   int64_t T, const int32_t* owner, const int32_t* partner, uint64_t* cost) {
     uint64_t* f = NULL;
@@ -306,7 +314,7 @@ int or_task_costs(int model, int fn, int32_t piece, int32_t c_task, int32_t c_ow
         uint64_t dhp = (uint64_t)(off[p + 1] - off[p]);
         int last = (t + 1 == T) || owner[t + 1] != o;
         if (model == OR_MODEL_EDGE) {
-            uint64_t pieces = (dho + (uint64_t)piece - 1) / (uint64_t)piece;
+            uint64_t pieces = dho <= (uint64_t)small_max ? 1 : (dho + (uint64_t)piece - 1) / (uint64_t)piece;
             cost[t] = pieces * (dhp + (uint64_t)c_task);
             if (last) cost[t] += dho + (uint64_t)c_owner;
         } else if (model == OR_MODEL_MERGE) {

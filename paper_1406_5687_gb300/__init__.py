@@ -169,8 +169,9 @@ class Graph:
                  timing: bool = False):
         """Count with explicit options; optionally record the schedule.
 
-        Returns (T, meta, chunks, busy): chunks is an int64 CUDA tensor of shape (k, 4)
-        holding (cost_lo, cost_hi, task_lo, task_hi) per chunk taken; busy is (W, 2).
+        Returns (T, meta, chunks, busy): chunks is an int64 CUDA tensor of shape (k, 5)
+        holding (class, cost_lo, cost_hi, task_lo, task_hi) per chunk taken, costs counted
+        within the class; busy is (W_small + W_big, 2): clock cycles and chunks per worker.
         """
         torch = _torch()
         tr = _lib.CountTrace()
@@ -181,17 +182,25 @@ class Graph:
             tr.cap = trace_cap
         if busy:
             sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-            bz = torch.zeros(2 * sms * 64, dtype=torch.int64, device="cuda")  # at most 64 resident warps per SM
+            # small-class warps (at most 64 resident per SM) plus big-class blocks (at most 32 per SM)
+            bz = torch.zeros(2 * sms * 96, dtype=torch.int64, device="cuda")
             tr.workers_busy = bz.data_ptr()
         t = ctypes.c_uint64()
         opt = ctypes.byref(options) if options is not None else None
         use_trace = trace_cap > 0 or busy or timing
         _lib.check(load().tc_count_ex(self._h, opt, _stream(stream), ctypes.byref(t),
                                       ctypes.byref(tr) if use_trace else None), "tc_count_ex")
-        meta = {"n_chunks": tr.n_chunks, "n_workers": tr.n_workers, "total_cost": tr.total_cost,
-                "min_chunk": tr.min_chunk, "prefix_ms": tr.prefix_ms, "kernel_ms": tr.kernel_ms}
-        chunks = ch.view(-1, 4)[:min(tr.n_chunks, trace_cap)] if ch is not None else None
-        busy_t = bz.view(-1, 2)[:tr.n_workers] if bz is not None else None
+        meta = {"n_chunks": tr.n_chunks, "n_workers": list(tr.n_workers), "total_cost": list(tr.total_cost),
+                "min_chunk": list(tr.min_chunk), "tasks_small": tr.tasks_small, "prefix_ms": tr.prefix_ms,
+                "kernel_small_ms": tr.kernel_small_ms, "kernel_big_ms": tr.kernel_big_ms,
+                "kernel_ms": tr.kernel_small_ms + tr.kernel_big_ms}
+        chunks = None
+        if ch is not None:
+            raw = ch.view(-1, 4)[:min(tr.n_chunks, trace_cap)]
+            cls = torch.bitwise_right_shift(raw[:, 0], 56)
+            lo = torch.bitwise_and(raw[:, 0], (1 << 56) - 1)
+            chunks = torch.stack([cls, lo, raw[:, 1], raw[:, 2], raw[:, 3]], dim=1)
+        busy_t = bz.view(-1, 2)[:tr.n_workers[0] + tr.n_workers[1]] if bz is not None else None
         return int(t.value), meta, chunks, busy_t
 
     def vertex_cost(self, fn: int, stream=None):

@@ -37,8 +37,10 @@ class TcError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("input_policy", ctypes.c_int32), ("cost_model", ctypes.c_int32), ("piece", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("big_warps", ctypes.c_int32), ("small_max", ctypes.c_int32),
                 ("static_percent", ctypes.c_int32), ("min_chunk", ctypes.c_int64), ("c_task", ctypes.c_int32),
-                ("c_owner", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64), ("retry_limit", ctypes.c_int64),
+                ("c_owner", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_int64), ("retry_limit", ctypes.c_int64),
                 ("alloc", ALLOC_FN), ("release", RELEASE_FN), ("alloc_ctx", ctypes.c_void_p)]
 
 
@@ -46,6 +48,7 @@ class GraphInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("max_degree", ctypes.c_int32), ("max_dhat", ctypes.c_int32),
                 ("id_bits", ctypes.c_int32), ("m_in", ctypes.c_int64), ("self_loops", ctypes.c_int64),
                 ("duplicates", ctypes.c_int64), ("m_hat", ctypes.c_int64), ("tasks", ctypes.c_int64),
+                ("tasks_small", ctypes.c_int64),
                 ("sum_dhat_v", ctypes.c_uint64), ("sum_dhat_u", ctypes.c_uint64), ("sum_stream", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_int64)]
 
@@ -55,8 +58,9 @@ class GraphInfo(ctypes.Structure):
 
 class CountTrace(ctypes.Structure):
     _fields_ = [("chunks", ctypes.c_void_p), ("cap", ctypes.c_int64), ("workers_busy", ctypes.c_void_p),
-                ("n_chunks", ctypes.c_int64), ("n_workers", ctypes.c_int64), ("total_cost", ctypes.c_uint64),
-                ("min_chunk", ctypes.c_uint64), ("prefix_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float)]
+                ("n_chunks", ctypes.c_int64), ("n_workers", ctypes.c_int64 * 2), ("total_cost", ctypes.c_uint64 * 2),
+                ("min_chunk", ctypes.c_uint64 * 2), ("tasks_small", ctypes.c_int64), ("prefix_ms", ctypes.c_float),
+                ("kernel_small_ms", ctypes.c_float), ("kernel_big_ms", ctypes.c_float), ("reserved", ctypes.c_float)]
 
 
 class Result(ctypes.Structure):

@@ -13,18 +13,23 @@ struct HandleDev {
     DevStatus status;
     unsigned long long result;
     long long pad;
-    Sched sched;
+    Sched sched[2];
 };
 
 tc_status check_options(const tc_options& o) {
     if (o.input_policy != TC_INPUT_SANITIZE && o.input_policy != TC_INPUT_STRICT) return TC_ERR_INVALID_ARG;
     if (o.cost_model < TC_COST_EDGE || o.cost_model > TC_COST_NEW) return TC_ERR_INVALID_ARG;
-    if (o.piece != 128 && o.piece != 256 && o.piece != 512 && o.piece != 1024 && o.piece != 2048)
+    if (o.piece != 256 && o.piece != 512 && o.piece != 1024 && o.piece != 2048 && o.piece != 4096)
         return TC_ERR_INVALID_ARG;
     if (o.warps_per_block != 1 && o.warps_per_block != 2 && o.warps_per_block != 4 && o.warps_per_block != 8 &&
         o.warps_per_block != 16)
         return TC_ERR_INVALID_ARG;
-    if ((size_t)o.warps_per_block * 2 * o.piece * 4 > 200 * 1024) return TC_ERR_INVALID_ARG;  // shared memory per block
+    if (o.big_warps != 4 && o.big_warps != 8 && o.big_warps != 16) return TC_ERR_INVALID_ARG;
+    if (o.small_max != 0 && o.small_max != 16 && o.small_max != 32 && o.small_max != 64 && o.small_max != 128 &&
+        o.small_max != 256)
+        return TC_ERR_INVALID_ARG;
+    // shared memory: the small kernel's per-warp tables, the big kernel's block table
+    if ((size_t)o.warps_per_block * small_table_slots(o.small_max) * 4 > 200 * 1024) return TC_ERR_INVALID_ARG;
     if (o.blocks_per_sm < 0 || o.static_percent < 0 || o.static_percent > 100) return TC_ERR_INVALID_ARG;
     if (o.min_chunk < 0 || o.c_task < 0 || o.c_owner < 0 || o.hbm_budget_bytes < 0 || o.retry_limit < 0)
         return TC_ERR_INVALID_ARG;
@@ -117,8 +122,10 @@ void tc_options_default(tc_options* o) {
     std::memset(o, 0, sizeof(*o));
     o->input_policy = TC_INPUT_SANITIZE;
     o->cost_model = TC_COST_EDGE;
-    o->piece = 1024;
+    o->piece = 2048;
     o->warps_per_block = 8;
+    o->big_warps = 16;
+    o->small_max = 64;
     o->blocks_per_sm = 0;
     o->static_percent = 50;
     o->min_chunk = 0;
@@ -162,7 +169,7 @@ tc_status tc_build(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
             g->status = (DevStatus*)p;
             HandleDev* hd = (HandleDev*)p;
             g->work.result = &hd->result;
-            g->work.sched = &hd->sched;
+            g->work.sched = hd->sched;
             if (cudaMemsetAsync(p, 0, sizeof(HandleDev), s) != cudaSuccess) st = TC_ERR_CUDA;
         }
     }
@@ -257,6 +264,7 @@ tc_status tc_graph_get_info(tc_graph_t g, tc_graph_info* info) {
     info->duplicates = g->duplicates;
     info->m_hat = g->m_hat;
     info->tasks = g->tasks;
+    info->tasks_small = g->tasks_small;
     info->sum_dhat_v = g->sum_dhat_v;
     info->sum_dhat_u = g->sum_dhat_u;
     info->sum_stream = g->sum_stream;

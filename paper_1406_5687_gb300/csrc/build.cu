@@ -201,11 +201,13 @@ __global__ void k_max_deg(const int32_t* __restrict__ deg, const int32_t* __rest
 }
 
 // --------------------------------------------------------------------------- tasks
+// Task key: (class << 2b) | (owner << b) | partner, class 1 when the owner's list has more
+// than small_max entries, so that the sort puts every small task first.
 __global__ void k_task_keys(const uint64_t* __restrict__ okeys, const int32_t* __restrict__ cols, int64_t mh, int b,
-                            const int32_t* __restrict__ dhat, uint64_t sent, uint64_t* __restrict__ tkeys,
-                            BuildCounters* cnt) {
+                            const int32_t* __restrict__ dhat, int small_max, uint64_t sent,
+                            uint64_t* __restrict__ tkeys, BuildCounters* cnt) {
     const int lane = threadIdx.x & 31;
-    unsigned long long sv = 0, su = 0, ss = 0, nt = 0;
+    unsigned long long sv = 0, su = 0, ss = 0, nt = 0, nsm = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mh; i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t v = (uint32_t)(okeys[i] >> b);
         uint32_t u = (uint32_t)cols[i];
@@ -215,9 +217,12 @@ __global__ void k_task_keys(const uint64_t* __restrict__ okeys, const int32_t* _
         sv += (unsigned long long)dv;
         su += (unsigned long long)du;
         if (dp > 0) {
+            const int32_t dop = dv >= du ? dv : du;
+            const uint64_t big = dop > small_max ? 1ull : 0ull;
             ss += (unsigned long long)dp;
             nt += 1;
-            tkeys[i] = ((uint64_t)o << b) | p;
+            nsm += 1ull - big;
+            tkeys[i] = (big << (2 * b)) | ((uint64_t)o << b) | p;
         } else {
             tkeys[i] = sent;
         }
@@ -226,11 +231,13 @@ __global__ void k_task_keys(const uint64_t* __restrict__ okeys, const int32_t* _
     su = warp_sum(su);
     ss = warp_sum(ss);
     nt = warp_sum(nt);
+    nsm = warp_sum(nsm);
     if (lane == 0) {
         if (sv) atomicAdd(&cnt->sum_dhat_v, sv);
         if (su) atomicAdd(&cnt->sum_dhat_u, su);
         if (ss) atomicAdd(&cnt->sum_stream, ss);
         if (nt) atomicAdd(&cnt->tasks, nt);
+        if (nsm) atomicAdd(&cnt->tasks_small, nsm);
     }
 }
 
@@ -239,7 +246,7 @@ __global__ void k_task_records(const uint64_t* __restrict__ tkeys, int64_t T, in
     const uint64_t mask = (1ull << b) - 1;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
         uint64_t k = tkeys[t];
-        uint32_t o = (uint32_t)(k >> b), p = (uint32_t)(k & mask);
+        uint32_t o = (uint32_t)((k >> b) & mask), p = (uint32_t)(k & mask);
         int64_t s = off[p], e = off[p + 1];
         TaskRec r;
         r.owner = o;
@@ -358,14 +365,16 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     TC_CUDA_TRY(cudaGetLastError());
 
     // tasks
+    // task keys carry one more bit (the class); their sentinel is all ones over 2b + 1 bits
+    const uint64_t tsent = (1ull << (nbits + 1)) - 1;
     if (mh > 0) {
-        k_task_keys<<<grid_stride_blocks(mh), kThreads, 0, s>>>(osorted, cols.ptr, mh, b, dhat.ptr, sent,
-                                                                             free_buf, cnt.ptr);
+        k_task_keys<<<grid_stride_blocks(mh), kThreads, 0, s>>>(osorted, cols.ptr, mh, b, dhat.ptr,
+                                                                g->opt.small_max, tsent, free_buf, cnt.ptr);
         note_launch();
     }
     TC_CUDA_TRY(cudaGetLastError());
     uint64_t* tsorted = nullptr;
-    TC_TRY(radix_sort_u64(free_buf, osorted, mh, nbits, al, s, &tsorted));
+    TC_TRY(radix_sort_u64(free_buf, osorted, mh, nbits + 1, al, s, &tsorted));
     TC_CUDA_TRY(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(hc), cudaMemcpyDeviceToHost, s));
     TC_CUDA_TRY(cudaStreamSynchronize(s));
     const int64_t T = (int64_t)hc.tasks;
@@ -378,6 +387,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     TC_CUDA_TRY(cudaGetLastError());
 
     g->tasks = T;
+    g->tasks_small = (int64_t)hc.tasks_small;
     g->max_degree = hc.max_degree;
     g->max_dhat = hc.max_dhat;
     g->sum_dhat_v = hc.sum_dhat_v;

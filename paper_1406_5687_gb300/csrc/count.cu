@@ -1,18 +1,26 @@
 // count.cu -- steps a6-a8: task costs and their prefix, the Eq. 1 / Eq. 2 schedule, the
-// persistent intersection kernel and the exact reduction.
+// persistent intersection kernels and the exact reduction.
 //
 // Work unit.  Fig. 1 sums |N_v ∩ N_u| over oriented edges (v,u).  Each oriented edge is one
-// task owned by the endpoint whose list is longer; the owner's list is staged once into a
-// per-warp open-addressing hash table in shared memory, and the partner lists of all the
-// owner's tasks are streamed through it, 32 list entries per warp step.  So each edge costs
-// min(|N_v|, |N_u|) streamed entries instead of the |N_v| + |N_u| of a merge (Sec. III-A).
+// task owned by the endpoint whose list is longer; the owner's list is staged into an
+// open-addressing hash table in shared memory (load at most 1/8, so a lookup almost
+// always ends at its first or second slot) and the partner lists of the owner's tasks are
+// streamed through it.  Each edge thus costs min(|N_v|, |N_u|) streamed entries instead of
+// the |N_v| + |N_u| of a merge (Sec. III-A).
 //
-// Schedule (Sec. V-B).  The persistent grid has W warps ("workers").  Task costs are
-// prefix-summed (uint64).  The first H = floor(C * static_percent / 100) cost units (Eq. 1,
-// default one half) are split into W equal initial chunks, one per warp, taken without any
-// coordination; the rest is handed out by a compare-and-swap on a device head: each pop
-// takes max(min_chunk, floor((C - head) / W)) (Eq. 2), so chunks shrink as the work drains.
-// A cost boundary maps to the first task whose exclusive prefix reaches it.
+// Two task classes, two kernels.  Owners with at most small_max entries are counted by one
+// warp each (a table per warp); longer owners by a whole block whose warps share one table
+// and pull batches of 32 tasks from a block counter.  Inside a batch, partner lists of 32
+// or more entries are streamed by the whole warp one list at a time; shorter ones are
+// concatenated and spread over the lanes.
+//
+// Schedule (Sec. V-B), per class.  The persistent grid has W workers (warps for the small
+// class, blocks for the big one).  Task costs are prefix-summed (uint64).  The first
+// H = floor(C * static_percent / 100) cost units (Eq. 1, default one half) are split into W
+// equal initial chunks, one per worker, taken without coordination; the rest is handed out
+// by a compare-and-swap on a device head, each pop taking max(min_chunk,
+// floor((C - head) / W)) (Eq. 2), so chunks shrink as the work drains.  A cost boundary maps
+// to the first task whose exclusive prefix reaches it.
 //
 // Reduction.  Each warp sums its hits in registers, then one uint64 atomicAdd per warp:
 // exact and independent of order.
@@ -29,11 +37,13 @@ struct CountArgs {
     const int64_t* off;
     const int32_t* cols;
     const TaskRec* tasks;
-    long long T;
+    long long t_begin, t_end;  // this class's tasks
     const int32_t* deg;
-    const uint64_t* P;  // T + 1 exclusive prefix of task costs
-    Sched* sched;
+    const uint64_t* P;   // exclusive prefix of all task costs (T + 1)
+    Sched* sched;        // this class's schedule
+    Sched* trace_sched;  // holds the shared trace record counter
     long long W;
+    int cls;
     int piece;
     int table_slots;
     int warps_per_block;
@@ -43,47 +53,52 @@ struct CountArgs {
     uint64_t* trace_chunks;
     long long trace_cap;
     uint64_t* trace_busy;
+    long long busy_offset;
     DevStatus* status;
     long long retry_limit;
 };
 
-// First t in [0, T] with P[t] >= x, given P[T] >= x.  32-way search: each round every lane
-// samples one position and the warp keeps the gap between the last sample below x and the
-// first at or above it.
-__device__ __forceinline__ long long warp_lower_bound(const uint64_t* __restrict__ P, long long T,
-                                                      unsigned long long x, int lane) {
-    long long lo = 0, hi = T;  // invariant: P[lo-1] < x (or lo = 0), P[hi] >= x
+// First index q in [lo, hi] with pred(q), for pred false..false true..true and pred(hi) true.
+// Each round every lane tests one sample and the warp keeps the gap between the last false
+// and the first true sample, so a range of R shrinks to R/32.
+template <class Pred>
+__device__ __forceinline__ long long warp_first_true(long long lo, long long hi, Pred pred, int lane) {
     while (hi - lo > 31) {
         const long long step = (hi - lo + 31) / 32;
         long long q = lo + (long long)lane * step;
         if (q > hi) q = hi;
-        const unsigned b = __ballot_sync(kFull, P[q] >= x);
+        const unsigned b = __ballot_sync(kFull, pred(q));
         if (b == 0) {
-            long long q31 = lo + 31 * step;
+            const long long q31 = lo + 31 * step;
             lo = (q31 > hi ? hi : q31) + 1;
         } else {
             const int f = __ffs(b) - 1;
             if (f == 0) return lo;
-            long long qf = lo + (long long)f * step;
+            const long long qf = lo + (long long)f * step;
             hi = qf > hi ? hi : qf;
             lo = lo + (long long)(f - 1) * step + 1;
         }
     }
     const long long q = lo + lane;
-    const unsigned b = __ballot_sync(kFull, q <= hi ? (P[q] >= x) : true);
+    const unsigned b = __ballot_sync(kFull, q <= hi ? pred(q) : true);
     return lo + (__ffs(b) - 1);
 }
 
-__device__ __forceinline__ long long map_bound(const CountArgs& a, unsigned long long x, unsigned long long C,
-                                               int lane) {
-    return x >= C ? a.T : warp_lower_bound(a.P, a.T, x, lane);
+// Cost boundary x (class-local) -> task index: the first task of the class whose exclusive
+// prefix reaches x; x >= C maps to the end of the class.
+__device__ __forceinline__ long long class_bound(const CountArgs& a, unsigned long long x, unsigned long long C,
+                                                 unsigned long long base, int lane) {
+    if (x >= C) return a.t_end;
+    const uint64_t* __restrict__ P = a.P;
+    const unsigned long long target = x + base;
+    return warp_first_true(a.t_begin, a.t_end, [&](long long q) { return P[q] >= target; }, lane);
 }
 
 // Position of u in the sorted list N+(v).
 __device__ __forceinline__ long long edge_position(const CountArgs& a, uint32_t v, uint32_t u) {
     long long lo = a.off[v], hi = a.off[v + 1];
     while (lo < hi) {
-        long long mid = (lo + hi) >> 1;
+        const long long mid = (lo + hi) >> 1;
         if ((uint32_t)a.cols[mid] < u) lo = mid + 1; else hi = mid;
     }
     return lo;
@@ -106,110 +121,213 @@ __device__ __forceinline__ void on_hit(const CountArgs& a, uint32_t owner, uint3
     }
 }
 
-// Count the tasks [t0, t1) (uniform across the warp).
+struct HashView {
+    uint32_t* tbl;
+    uint32_t cmask;
+    int shift;
+};
+
+// Table of `cap` slots (a power of two) for a list of at most cap / 8 entries.
+__device__ __forceinline__ HashView make_view(uint32_t* tbl, uint32_t cap) {
+    HashView hv;
+    hv.tbl = tbl;
+    hv.cmask = cap - 1;
+    hv.shift = 33 - __ffs(cap);  // 32 - log2(cap)
+    return hv;
+}
+
+__device__ __forceinline__ void hash_insert(const HashView& hv, uint32_t x) {
+    uint32_t h = (x * kHashMul) >> hv.shift;
+    while (atomicCAS(&hv.tbl[h], kEmpty, x) != kEmpty) h = (h + 1) & hv.cmask;
+}
+
+__device__ __forceinline__ bool hash_probe(const HashView& hv, uint32_t w) {
+    uint32_t h = (w * kHashMul) >> hv.shift;
+    for (;;) {
+        const uint32_t s = hv.tbl[h];
+        if (s == w) return true;
+        if (s == kEmpty) return false;
+        h = (h + 1) & hv.cmask;
+    }
+}
+
+// Bit position of the set bit of m that has exactly k set bits below it (0 <= k < popc(m)):
+// halve the window five times, skipping the low half when the target is above it.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (k >= c) {
+            k -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+// One warp counts a batch of nb <= 32 tasks of `owner` (lane i holds task i's record)
+// against the owner's staged table.
 template <bool EXTRA>
-__device__ void process_range(const CountArgs& a, long long t0, long long t1, uint32_t* __restrict__ tbl, int lane,
+__device__ void warp_batch(const CountArgs& a, const TaskRec& r, int nb, uint32_t owner, const HashView& hv,
+                           int lane, unsigned long long& acc) {
+    const uint32_t len = lane < nb ? r.plen : 0u;
+    // partner lists of 32 or more entries: the whole warp streams one list at a time
+    unsigned longm = __ballot_sync(kFull, len >= 32u);
+    while (longm) {
+        const int j = __ffs(longm) - 1;
+        longm &= longm - 1;
+        const uint32_t s = __shfl_sync(kFull, r.pstart, j);
+        const uint32_t L = __shfl_sync(kFull, len, j);
+        uint32_t pj = 0;
+        if (EXTRA) pj = __shfl_sync(kFull, r.partner, j);
+        const int32_t* __restrict__ lst = a.cols + s;
+        for (uint32_t base = 0; base < L; base += 32u * kUnroll) {
+            uint32_t wv[kUnroll];
+            bool ok[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const uint32_t i = base + 32u * u + lane;
+                ok[u] = i < L;
+                wv[u] = ok[u] ? (uint32_t)__ldg(lst + i) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const bool hit = ok[u] && hash_probe(hv, wv[u]);
+                acc += hit ? 1ull : 0ull;
+                if (EXTRA && hit) on_hit<EXTRA>(a, owner, pj, wv[u]);
+            }
+        }
+    }
+    // shorter lists: gather them into lanes 0..ns-1, then concatenate their entries and
+    // spread them over the lanes
+    const uint32_t short_len = len < 32u ? len : 0u;
+    const unsigned smask = __ballot_sync(kFull, short_len != 0u);
+    if (smask == 0u) return;
+    const int ns = __popc(smask);
+    const int src = lane < ns ? nth_set_bit(smask, lane) : 0;
+    const uint32_t g_len = __shfl_sync(kFull, short_len, src);
+    const uint32_t g_start = __shfl_sync(kFull, r.pstart, src);
+    uint32_t g_partner = 0;
+    if (EXTRA) g_partner = __shfl_sync(kFull, r.partner, src);
+    const uint32_t slen = lane < ns ? g_len : 0u;
+    const uint32_t incl = warp_inclusive_scan(slen, lane);
+    const uint32_t excl = incl - slen;
+    const uint32_t tot = __shfl_sync(kFull, incl, 31);
+    uint32_t before = 0;  // tasks whose entries start before the current window
+    for (uint32_t base = 0; base < tot; base += 32u * kUnroll) {
+        uint32_t wv[kUnroll];
+        bool ok[kUnroll];
+        int qj[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const uint32_t wb = base + 32u * u;
+            const uint32_t rel = excl - wb;
+            const uint32_t bit = (slen != 0u && rel < 32u) ? (1u << rel) : 0u;
+            const uint32_t starts = __reduce_or_sync(kFull, bit);
+            // entry g = wb + lane belongs to the last gathered task whose first entry is at or
+            // before g; gathered task k sits in lane k
+            const int q = ((int)(before + __popc(starts & lanemask_le())) - 1) & 31;
+            const uint32_t sj = __shfl_sync(kFull, g_start, q);
+            const uint32_t ej = __shfl_sync(kFull, excl, q);
+            const uint32_t g = wb + lane;
+            ok[u] = g < tot;
+            wv[u] = ok[u] ? (uint32_t)__ldg(&a.cols[(long long)sj + (g - ej)]) : 0u;
+            qj[u] = q;
+            before += __popc(starts);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const bool hit = ok[u] && hash_probe(hv, wv[u]);
+            acc += hit ? 1ull : 0ull;
+            if (EXTRA) {
+                const uint32_t pj = __shfl_sync(kFull, g_partner, qj[u]);
+                if (hit) on_hit<EXTRA>(a, owner, pj, wv[u]);
+            }
+        }
+    }
+}
+
+// Eq. 2: take the next chunk of the class's remaining cost (one thread; bounded retries).
+__device__ __forceinline__ int pop_chunk(const CountArgs& a, unsigned long long C, unsigned long long minc,
+                                         unsigned long long& c, unsigned long long& e) {
+    const unsigned long long W = (unsigned long long)a.W;
+    c = *(volatile unsigned long long*)&a.sched->head;
+    for (long long tries = 0;; ++tries) {
+        if (c >= C) return 0;
+        unsigned long long sz = (C - c) / W;
+        if (sz < minc) sz = minc;
+        e = (C - c > sz) ? c + sz : C;
+        const unsigned long long old = atomicCAS(&a.sched->head, c, e);
+        if (old == c) return 1;
+        c = old;
+        if (tries >= a.retry_limit) {
+            set_error(a.status, TC_ERR_TIMEOUT, tries);
+            return 0;
+        }
+    }
+}
+
+__device__ __forceinline__ void trace_chunk(const CountArgs& a, unsigned long long lo, unsigned long long hi,
+                                            long long t0, long long t1) {
+    if (!a.trace_chunks) return;
+    const unsigned long long idx = atomicAdd(&a.trace_sched->n_chunks, 1ull);
+    if ((long long)idx < a.trace_cap) {
+        a.trace_chunks[4 * idx] = ((uint64_t)a.cls << 56) | lo;
+        a.trace_chunks[4 * idx + 1] = hi;
+        a.trace_chunks[4 * idx + 2] = (uint64_t)t0;
+        a.trace_chunks[4 * idx + 3] = (uint64_t)t1;
+    }
+}
+
+// ------------------------------------------------------------------ small owners: one warp each
+
+template <bool EXTRA>
+__device__ void process_small(const CountArgs& a, long long t0, long long t1, uint32_t* __restrict__ tbl, int lane,
                               unsigned long long& acc) {
     long long t = t0;
     while (t < t1) {
         const uint32_t owner = a.tasks[t].owner;
         const long long obase = a.off[owner];
         const uint32_t olen = (uint32_t)(a.off[owner + 1] - obase);
-        long long seg_end = -1;  // end of this owner's tasks, found while probing the first piece
-        for (uint32_t ps = 0; ps < olen; ps += (uint32_t)a.piece) {
-            const uint32_t pl = min((uint32_t)a.piece, olen - ps);
-            uint32_t cap = 64;
-            while (cap < 2 * pl) cap <<= 1;
-            const int shift = 33 - __ffs(cap);  // 32 - log2(cap)
-            const uint32_t cmask = cap - 1;
-            // stage the piece N+(owner)[ps, ps + pl) into the table
-            for (uint32_t i = lane; i < cap; i += 32) tbl[i] = kEmpty;
-            __syncwarp();
-            for (uint32_t i = lane; i < pl; i += 32) {
-                const uint32_t x = (uint32_t)__ldg(&a.cols[obase + ps + i]);
-                uint32_t h = (x * kHashMul) >> shift;
-                while (atomicCAS(&tbl[h], kEmpty, x) != kEmpty) h = (h + 1) & cmask;
+        uint32_t cap = 32;
+        while (cap < 8 * olen) cap <<= 1;
+        const HashView hv = make_view(tbl, cap);
+        for (uint32_t i = lane; i < cap; i += 32) tbl[i] = kEmpty;
+        __syncwarp();
+        for (uint32_t i = lane; i < olen; i += 32) hash_insert(hv, (uint32_t)__ldg(&a.cols[obase + i]));
+        __syncwarp();
+        long long tt = t;
+        for (;;) {
+            const long long j = tt + lane;
+            TaskRec r = {0u, 0u, 0u, 0u};
+            bool valid = false;
+            if (j < t1) {
+                r = a.tasks[j];
+                valid = r.owner == owner;
             }
-            __syncwarp();
-            // stream the partner lists of the owner's tasks, 32 tasks per batch
-            long long tt = t;
-            for (;;) {
-                const long long lim = seg_end >= 0 ? seg_end : t1;
-                if (tt >= lim) break;
-                const long long j = tt + lane;
-                TaskRec r = {0u, 0u, 0u, 0u};
-                bool valid = false;
-                if (j < lim) {
-                    r = a.tasks[j];
-                    valid = seg_end >= 0 || r.owner == owner;
-                }
-                const unsigned vb = __ballot_sync(kFull, valid);
-                const int nb = (vb == kFull) ? 32 : __ffs(~vb) - 1;  // leading run of this owner's tasks
-                const uint32_t len = lane < nb ? r.plen : 0u;
-                const uint32_t start = r.pstart;
-                const uint32_t incl = warp_inclusive_scan(len, lane);
-                const uint32_t excl = incl - len;
-                const uint32_t tot = __shfl_sync(kFull, incl, 31);
-                uint32_t before = 0;  // tasks of the batch that start before the current window
-                for (uint32_t base = 0; base < tot; base += 32 * kUnroll) {
-                    uint32_t wv[kUnroll];
-                    bool ok[kUnroll];
-                    int qj[kUnroll];
-#pragma unroll
-                    for (int uu = 0; uu < kUnroll; ++uu) {
-                        const uint32_t wb = base + 32u * uu;
-                        const uint32_t rel = excl - wb;
-                        const uint32_t bit = (len != 0u && rel < 32u) ? (1u << rel) : 0u;
-                        const uint32_t starts = __reduce_or_sync(kFull, bit);
-                        const int q = ((int)(before + __popc(starts & lanemask_le())) - 1) & 31;
-                        const uint32_t sj = __shfl_sync(kFull, start, q);
-                        const uint32_t ej = __shfl_sync(kFull, excl, q);
-                        const uint32_t g = wb + lane;
-                        ok[uu] = g < tot;
-                        wv[uu] = ok[uu] ? (uint32_t)__ldg(&a.cols[(long long)sj + (g - ej)]) : 0u;
-                        qj[uu] = q;
-                        before += __popc(starts);
-                    }
-#pragma unroll
-                    for (int uu = 0; uu < kUnroll; ++uu) {
-                        bool hit = false;
-                        if (ok[uu]) {
-                            const uint32_t w = wv[uu];
-                            uint32_t h = (w * kHashMul) >> shift;
-                            for (;;) {
-                                const uint32_t s = tbl[h];
-                                if (s == w) { hit = true; break; }
-                                if (s == kEmpty) break;
-                                h = (h + 1) & cmask;
-                            }
-                        }
-                        acc += hit ? 1ull : 0ull;
-                        if (EXTRA) {
-                            const uint32_t pj = __shfl_sync(kFull, r.partner, qj[uu]);
-                            if (hit) on_hit<EXTRA>(a, owner, pj, wv[uu]);
-                        }
-                    }
-                }
-                if (nb < 32) {
-                    seg_end = tt + nb;
-                    break;
-                }
-                tt += 32;
+            const unsigned vb = __ballot_sync(kFull, valid);
+            const int nb = (vb == kFull) ? 32 : __ffs(~vb) - 1;  // leading run of this owner's tasks
+            warp_batch<EXTRA>(a, r, nb, owner, hv, lane, acc);
+            if (nb < 32) {
+                tt += nb;
+                break;
             }
-            if (seg_end < 0) seg_end = t1;
-            __syncwarp();
+            tt += 32;
         }
-        t = seg_end;
+        __syncwarp();
+        t = tt;
     }
 }
 
 template <bool EXTRA>
-__global__ void __launch_bounds__(512) k_count(CountArgs a) {
+__global__ void __launch_bounds__(512) k_count_small(CountArgs a) {
     extern __shared__ uint32_t smem_tbl[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const long long wid = (long long)blockIdx.x * a.warps_per_block + wib;
     uint32_t* tbl = smem_tbl + (size_t)wib * a.table_slots;
-    const unsigned long long C = a.sched->C, H = a.sched->H, minc = a.sched->min_chunk;
+    const unsigned long long C = a.sched->C, H = a.sched->H, minc = a.sched->min_chunk, base = a.sched->base;
     const unsigned long long W = (unsigned long long)a.W;
     unsigned long long acc = 0;
     long long busy = 0, nch = 0;
@@ -218,61 +336,27 @@ __global__ void __launch_bounds__(512) k_count(CountArgs a) {
         const unsigned long long q = H / W, r = H % W, w0 = (unsigned long long)wid;
         const unsigned long long lo = w0 * q + (w0 < r ? w0 : r);
         const unsigned long long hi = (w0 + 1) * q + (w0 + 1 < r ? w0 + 1 : r);
-        long long t0 = wid == 0 ? 0 : map_bound(a, lo, C, lane);
-        long long t1 = map_bound(a, hi, C, lane);
+        long long t0 = wid == 0 ? a.t_begin : class_bound(a, lo, C, base, lane);
+        long long t1 = class_bound(a, hi, C, base, lane);
+        if (lane == 0) trace_chunk(a, lo, hi, t0, t1);
         long long c0 = clock64();
-        if (a.trace_chunks && lane == 0) {
-            unsigned long long idx = atomicAdd(&a.sched->n_chunks, 1ull);
-            if ((long long)idx < a.trace_cap) {
-                a.trace_chunks[4 * idx] = lo;
-                a.trace_chunks[4 * idx + 1] = hi;
-                a.trace_chunks[4 * idx + 2] = (uint64_t)t0;
-                a.trace_chunks[4 * idx + 3] = (uint64_t)t1;
-            }
-        }
-        process_range<EXTRA>(a, t0, t1, tbl, lane, acc);
+        process_small<EXTRA>(a, t0, t1, tbl, lane, acc);
         busy += clock64() - c0;
         ++nch;
         // Eq. 2: guided chunks of the remaining cost
         for (;;) {
             unsigned long long c = 0, e = 0;
             int got = 0;
-            if (lane == 0) {
-                c = *(volatile unsigned long long*)&a.sched->head;
-                for (long long tries = 0;; ++tries) {
-                    if (c >= C) break;
-                    unsigned long long sz = (C - c) / W;
-                    if (sz < minc) sz = minc;
-                    e = (C - c > sz) ? c + sz : C;
-                    const unsigned long long old = atomicCAS(&a.sched->head, c, e);
-                    if (old == c) {
-                        got = 1;
-                        break;
-                    }
-                    c = old;
-                    if (tries >= a.retry_limit) {
-                        set_error(a.status, TC_ERR_TIMEOUT, tries);
-                        break;
-                    }
-                }
-            }
+            if (lane == 0) got = pop_chunk(a, C, minc, c, e);
             got = __shfl_sync(kFull, got, 0);
             if (!got) break;
             c = __shfl_sync(kFull, c, 0);
             e = __shfl_sync(kFull, e, 0);
-            t0 = map_bound(a, c, C, lane);
-            t1 = map_bound(a, e, C, lane);
+            t0 = class_bound(a, c, C, base, lane);
+            t1 = class_bound(a, e, C, base, lane);
+            if (lane == 0) trace_chunk(a, c, e, t0, t1);
             c0 = clock64();
-            if (a.trace_chunks && lane == 0) {
-                unsigned long long idx = atomicAdd(&a.sched->n_chunks, 1ull);
-                if ((long long)idx < a.trace_cap) {
-                    a.trace_chunks[4 * idx] = c;
-                    a.trace_chunks[4 * idx + 1] = e;
-                    a.trace_chunks[4 * idx + 2] = (uint64_t)t0;
-                    a.trace_chunks[4 * idx + 3] = (uint64_t)t1;
-                }
-            }
-            process_range<EXTRA>(a, t0, t1, tbl, lane, acc);
+            process_small<EXTRA>(a, t0, t1, tbl, lane, acc);
             busy += clock64() - c0;
             ++nch;
         }
@@ -281,9 +365,122 @@ __global__ void __launch_bounds__(512) k_count(CountArgs a) {
     if (lane == 0) {
         if (acc) atomicAdd(a.total, acc);
         if (a.trace_busy && wid < a.W) {
-            a.trace_busy[2 * wid] = (uint64_t)busy;
-            a.trace_busy[2 * wid + 1] = (uint64_t)nch;
+            a.trace_busy[2 * (a.busy_offset + wid)] = (uint64_t)busy;
+            a.trace_busy[2 * (a.busy_offset + wid) + 1] = (uint64_t)nch;
         }
+    }
+}
+
+// ------------------------------------------------------------------ big owners: one block each
+
+template <bool EXTRA>
+__device__ void process_big(const CountArgs& a, long long t0, long long t1, uint32_t* __restrict__ tbl,
+                            long long* s_seg, unsigned* s_next, int lane, int warp, unsigned long long& acc) {
+    long long t = t0;
+    while (t < t1) {
+        const uint32_t owner = a.tasks[t].owner;
+        if (warp == 0) {
+            const TaskRec* __restrict__ tk = a.tasks;
+            const long long e =
+                warp_first_true(t + 1, t1, [&](long long q) { return q >= t1 || tk[q].owner != owner; }, lane);
+            if (lane == 0) *s_seg = e;
+        }
+        const long long obase = a.off[owner];
+        const uint32_t olen = (uint32_t)(a.off[owner + 1] - obase);
+        __syncthreads();
+        const long long seg_end = *s_seg;
+        for (uint32_t ps = 0; ps < olen; ps += (uint32_t)a.piece) {
+            const uint32_t pl = min((uint32_t)a.piece, olen - ps);
+            uint32_t cap = 256;
+            while (cap < 8 * pl) cap <<= 1;
+            const HashView hv = make_view(tbl, cap);
+            for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) tbl[i] = kEmpty;
+            if (threadIdx.x == 0) *s_next = 0;
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < pl; i += blockDim.x)
+                hash_insert(hv, (uint32_t)__ldg(&a.cols[obase + ps + i]));
+            __syncthreads();
+            // the block's warps pull batches of 32 of the owner's tasks
+            for (;;) {
+                unsigned b = 0;
+                if (lane == 0) b = atomicAdd(s_next, 1u);
+                b = __shfl_sync(kFull, b, 0);
+                const long long tb = t + (long long)b * 32;
+                if (tb >= seg_end) break;
+                const int nb = (int)(seg_end - tb < 32 ? seg_end - tb : 32);
+                TaskRec r = {0u, 0u, 0u, 0u};
+                if (lane < nb) r = a.tasks[tb + lane];
+                warp_batch<EXTRA>(a, r, nb, owner, hv, lane, acc);
+            }
+            __syncthreads();
+        }
+        t = seg_end;
+    }
+}
+
+template <bool EXTRA>
+__global__ void __launch_bounds__(512, 2) k_count_big(CountArgs a) {
+    extern __shared__ uint32_t smem_tbl[];
+    __shared__ long long s_t[2];
+    __shared__ unsigned long long s_c[2];
+    __shared__ long long s_seg;
+    __shared__ unsigned s_next;
+    __shared__ int s_got;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long wid = blockIdx.x;
+    const unsigned long long C = a.sched->C, H = a.sched->H, minc = a.sched->min_chunk, base = a.sched->base;
+    const unsigned long long W = (unsigned long long)a.W;
+    unsigned long long acc = 0;
+    long long busy = 0, nch = 0;
+    // Eq. 1: the initial share split into W parts of equal cost, one per block
+    if (warp == 0) {
+        const unsigned long long q = H / W, r = H % W, w0 = (unsigned long long)wid;
+        const unsigned long long lo = w0 * q + (w0 < r ? w0 : r);
+        const unsigned long long hi = (w0 + 1) * q + (w0 + 1 < r ? w0 + 1 : r);
+        const long long t0 = wid == 0 ? a.t_begin : class_bound(a, lo, C, base, lane);
+        const long long t1 = class_bound(a, hi, C, base, lane);
+        if (lane == 0) {
+            s_t[0] = t0;
+            s_t[1] = t1;
+            trace_chunk(a, lo, hi, t0, t1);
+        }
+    }
+    __syncthreads();
+    long long c0 = clock64();
+    process_big<EXTRA>(a, s_t[0], s_t[1], smem_tbl, &s_seg, &s_next, lane, warp, acc);
+    busy += clock64() - c0;
+    ++nch;
+    // Eq. 2: guided chunks of the remaining cost
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long c = 0, e = 0;
+            s_got = pop_chunk(a, C, minc, c, e);
+            s_c[0] = c;
+            s_c[1] = e;
+        }
+        __syncthreads();
+        if (!s_got) break;
+        if (warp == 0) {
+            const long long t0 = class_bound(a, s_c[0], C, base, lane);
+            const long long t1 = class_bound(a, s_c[1], C, base, lane);
+            if (lane == 0) {
+                s_t[0] = t0;
+                s_t[1] = t1;
+                trace_chunk(a, s_c[0], s_c[1], t0, t1);
+            }
+        }
+        __syncthreads();
+        c0 = clock64();
+        process_big<EXTRA>(a, s_t[0], s_t[1], smem_tbl, &s_seg, &s_next, lane, warp, acc);
+        busy += clock64() - c0;
+        ++nch;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0 && acc) atomicAdd(a.total, acc);
+    if (threadIdx.x == 0 && a.trace_busy) {
+        a.trace_busy[2 * (a.busy_offset + wid)] = (uint64_t)busy;
+        a.trace_busy[2 * (a.busy_offset + wid) + 1] = (uint64_t)nch;
     }
 }
 
@@ -295,13 +492,13 @@ struct TaskCost {
     const int64_t* off;
     const uint64_t* f;
     int model;
-    uint32_t piece, c_task, c_owner;
+    uint32_t piece, small_max, c_task, c_owner;
     __device__ uint64_t operator()(int64_t t) const {
         const TaskRec r = tasks[t];
         const bool last = (t + 1 == T) || tasks[t + 1].owner != r.owner;
         if (model == TC_COST_EDGE) {
             const uint64_t dho = (uint64_t)(off[r.owner + 1] - off[r.owner]);
-            const uint64_t pieces = (dho + piece - 1) / piece;
+            const uint64_t pieces = dho <= small_max ? 1ull : (dho + piece - 1) / piece;
             uint64_t c = pieces * ((uint64_t)r.plen + c_task);
             if (last) c += dho + c_owner;
             return c;
@@ -311,21 +508,27 @@ struct TaskCost {
     }
 };
 
-__global__ void k_sched_init(Sched* sc, const uint64_t* P, long long T, long long W, int static_percent,
-                             long long min_chunk) {
-    const unsigned long long C = P[T];
+// Schedule state of both classes: class 0 is tasks [0, Ts), class 1 is [Ts, T).
+__global__ void k_sched_init(Sched* sc, const uint64_t* P, long long Ts, long long T, long long W0, long long W1,
+                             int static_percent, long long min_chunk) {
     const unsigned long long sp = (unsigned long long)static_percent;
-    const unsigned long long H = (C / 100ull) * sp + ((C % 100ull) * sp) / 100ull;
-    unsigned long long minc = (unsigned long long)min_chunk;
-    if (min_chunk <= 0) {
-        minc = C / ((unsigned long long)W * 128ull);
-        if (minc < 32ull) minc = 32ull;
+    for (int c = 0; c < 2; ++c) {
+        const unsigned long long base = c == 0 ? 0ull : P[Ts];
+        const unsigned long long C = (c == 0 ? P[Ts] : P[T]) - base;
+        const unsigned long long W = (unsigned long long)(c == 0 ? W0 : W1);
+        const unsigned long long H = (C / 100ull) * sp + ((C % 100ull) * sp) / 100ull;
+        unsigned long long minc = (unsigned long long)min_chunk;
+        if (min_chunk <= 0) {
+            minc = C / (W * 128ull);
+            if (minc < 32ull) minc = 32ull;
+        }
+        sc[c].C = C;
+        sc[c].H = H;
+        sc[c].min_chunk = minc;
+        sc[c].head = H;
+        sc[c].n_chunks = 0;
+        sc[c].base = base;
     }
-    sc->C = C;
-    sc->H = H;
-    sc->min_chunk = minc;
-    sc->head = H;
-    sc->n_chunks = 0;
 }
 
 // Per-vertex cost functions (Sec. IV-B, IV-F, V-A); f must be zeroed for TC_FN_NEW.
@@ -389,12 +592,6 @@ tc_status clustering_enqueue(tc_graph* g, const uint64_t* t_v, double* cc, cudaS
 
 tc_status ensure_count_work(tc_graph* g, const tc_options& opt, cudaStream_t s) {
     CountWork& w = g->work;
-    if (!w.sched) {
-        void* p = nullptr;
-        TC_TRY(g->al.get(&p, sizeof(Sched) + 64, s));
-        w.sched = (Sched*)p;
-        g->bytes += (int64_t)align_up(sizeof(Sched) + 64, 256);
-    }
     if (!w.prefix) {
         void* p = nullptr;
         TC_TRY(g->al.get(&p, (size_t)(g->tasks + 1) * 8, s));
@@ -416,11 +613,14 @@ tc_status ensure_count_work(tc_graph* g, const tc_options& opt, cudaStream_t s) 
     return TC_OK;
 }
 
-template <bool EXTRA>
-static tc_status launch_count(const CountArgs& a, int blocks, int threads, size_t smem, cudaStream_t s) {
-    k_count<EXTRA><<<blocks, threads, smem, s>>>(a);
-    note_launch();
-    TC_CUDA_TRY(cudaGetLastError());
+template <class K>
+static tc_status grid_for_kernel(K kernel, int threads, size_t smem, int cap_per_sm, int* blocks) {
+    TC_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    TC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
+    if (per_sm < 1) return TC_ERR_INVALID_ARG;
+    if (cap_per_sm > 0 && cap_per_sm < per_sm) per_sm = cap_per_sm;
+    *blocks = num_sms() * per_sm;
     return TC_OK;
 }
 
@@ -429,57 +629,53 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     TC_TRY(ensure_count_work(g, opt, s));
     CountWork& w = g->work;
     const bool extra = t_v != nullptr || per_edge != nullptr;
+    const long long T = g->tasks, Ts = g->tasks_small;
+    // small class: warps with their own tables
     const int wpb = opt.warps_per_block;
-    const int threads = wpb * 32;
-    const int table_slots = 2 * opt.piece;
-    const size_t smem = (size_t)wpb * table_slots * sizeof(uint32_t);
-    // occupancy decides the persistent grid
-    int per_sm = 0;
+    const int slots_s = small_table_slots(g->opt.small_max);
+    const size_t smem_s = (size_t)wpb * slots_s * sizeof(uint32_t);
+    // big class: blocks sharing one table of 8 * piece slots
+    const int threads_b = opt.big_warps * 32;
+    const int slots_b = 8 * opt.piece;
+    const size_t smem_b = (size_t)slots_b * sizeof(uint32_t);
+    int blocks_s = 0, blocks_b = 0;
     if (extra) {
-        TC_CUDA_TRY(cudaFuncSetAttribute(k_count<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        TC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count<true>, threads, smem));
+        TC_TRY(grid_for_kernel(k_count_small<true>, wpb * 32, smem_s, opt.blocks_per_sm, &blocks_s));
+        TC_TRY(grid_for_kernel(k_count_big<true>, threads_b, smem_b, opt.blocks_per_sm, &blocks_b));
     } else {
-        TC_CUDA_TRY(cudaFuncSetAttribute(k_count<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        TC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count<false>, threads, smem));
+        TC_TRY(grid_for_kernel(k_count_small<false>, wpb * 32, smem_s, opt.blocks_per_sm, &blocks_s));
+        TC_TRY(grid_for_kernel(k_count_big<false>, threads_b, smem_b, opt.blocks_per_sm, &blocks_b));
     }
-    if (per_sm < 1) return TC_ERR_INVALID_ARG;
-    if (opt.blocks_per_sm > 0 && opt.blocks_per_sm < per_sm) per_sm = opt.blocks_per_sm;
-    const int blocks = num_sms() * per_sm;
-    const long long W = (long long)blocks * wpb;
+    const long long W_s = (long long)blocks_s * wpb, W_b = blocks_b;
 
-    // events around the two phases when a trace is requested (on the launching stream)
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     if (trace) {
         for (auto& e : ev) TC_CUDA_TRY(cudaEventCreate(&e));
         TC_CUDA_TRY(cudaEventRecord(ev[0], s));
     }
-    // a6: costs, prefix, schedule state
+    // a6: costs, prefix, schedule state of both classes
     if (opt.cost_model >= TC_COST_ONE) {
         const int fn = opt.cost_model - TC_COST_ONE;  // ONE, DEGREE, PATRIC, NEW in enum order
         TC_TRY(vertex_cost_enqueue(g, fn, s, w.fcost));
     }
-    TaskCost tcf{g->trec, g->tasks, g->off, w.fcost, opt.cost_model, (uint32_t)opt.piece, (uint32_t)opt.c_task,
-                 (uint32_t)opt.c_owner};
-    TC_CUDA_TRY(scan_exclusive(tcf, g->tasks, w.prefix, w.scan_scr, s));
-    k_sched_init<<<1, 1, 0, s>>>(w.sched, w.prefix, g->tasks, W, opt.static_percent, opt.min_chunk);
+    TaskCost tcf{g->trec, T, g->off, w.fcost, opt.cost_model, (uint32_t)opt.piece, (uint32_t)g->opt.small_max,
+                 (uint32_t)opt.c_task, (uint32_t)opt.c_owner};
+    TC_CUDA_TRY(scan_exclusive(tcf, T, w.prefix, w.scan_scr, s));
+    k_sched_init<<<1, 1, 0, s>>>(w.sched, w.prefix, Ts, T, W_s, W_b, opt.static_percent, opt.min_chunk);
     note_launch();
     TC_CUDA_TRY(cudaGetLastError());
     TC_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(unsigned long long), s));
     if (t_v && g->n > 0) TC_CUDA_TRY(cudaMemsetAsync(t_v, 0, sizeof(unsigned long long) * g->n, s));
     if (per_edge && g->m_hat > 0) TC_CUDA_TRY(cudaMemsetAsync(per_edge, 0, sizeof(uint32_t) * g->m_hat, s));
+    if (trace) TC_CUDA_TRY(cudaEventRecord(ev[1], s));
 
     CountArgs a;
     a.off = g->off;
     a.cols = g->cols;
     a.tasks = g->trec;
-    a.T = g->tasks;
     a.deg = g->deg;
     a.P = w.prefix;
-    a.sched = w.sched;
-    a.W = W;
-    a.piece = opt.piece;
-    a.table_slots = table_slots;
-    a.warps_per_block = wpb;
+    a.trace_sched = w.sched;
     a.total = total_dev;
     a.t_v = t_v;
     a.per_edge = per_edge;
@@ -488,25 +684,58 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     a.trace_busy = trace ? trace->workers_busy : nullptr;
     a.status = g->status;
     a.retry_limit = opt.retry_limit > 0 ? opt.retry_limit : (1ll << 24);
-    if (trace) TC_CUDA_TRY(cudaEventRecord(ev[1], s));
-    if (g->tasks > 0) {
-        if (extra) TC_TRY(launch_count<true>(a, blocks, threads, smem, s));
-        else TC_TRY(launch_count<false>(a, blocks, threads, smem, s));
+    // small class
+    a.t_begin = 0;
+    a.t_end = Ts;
+    a.sched = w.sched;
+    a.W = W_s;
+    a.cls = 0;
+    a.piece = opt.piece;
+    a.table_slots = slots_s;
+    a.warps_per_block = wpb;
+    a.busy_offset = 0;
+    if (Ts > 0) {
+        if (extra) k_count_small<true><<<blocks_s, wpb * 32, smem_s, s>>>(a);
+        else k_count_small<false><<<blocks_s, wpb * 32, smem_s, s>>>(a);
+        note_launch();
+        TC_CUDA_TRY(cudaGetLastError());
+    }
+    if (trace) TC_CUDA_TRY(cudaEventRecord(ev[2], s));
+    // big class
+    a.t_begin = Ts;
+    a.t_end = T;
+    a.sched = w.sched + 1;
+    a.W = W_b;
+    a.cls = 1;
+    a.table_slots = slots_b;
+    a.warps_per_block = opt.big_warps;
+    a.busy_offset = W_s;
+    if (T > Ts) {
+        if (extra) k_count_big<true><<<blocks_b, threads_b, smem_b, s>>>(a);
+        else k_count_big<false><<<blocks_b, threads_b, smem_b, s>>>(a);
+        note_launch();
+        TC_CUDA_TRY(cudaGetLastError());
     }
     if (trace) {
-        TC_CUDA_TRY(cudaEventRecord(ev[2], s));
-        Sched hs;
-        TC_CUDA_TRY(cudaMemcpyAsync(&hs, w.sched, sizeof(Sched), cudaMemcpyDeviceToHost, s));
+        TC_CUDA_TRY(cudaEventRecord(ev[3], s));
+        Sched hs[2];
+        TC_CUDA_TRY(cudaMemcpyAsync(hs, w.sched, sizeof(hs), cudaMemcpyDeviceToHost, s));
         TC_CUDA_TRY(cudaStreamSynchronize(s));
-        trace->n_chunks = (int64_t)hs.n_chunks;
-        trace->n_workers = W;
-        trace->total_cost = hs.C;
-        trace->min_chunk = hs.min_chunk;
+        trace->n_chunks = (int64_t)hs[0].n_chunks;
+        trace->n_workers[0] = W_s;
+        trace->n_workers[1] = W_b;
+        for (int c = 0; c < 2; ++c) {
+            trace->total_cost[c] = hs[c].C;
+            trace->min_chunk[c] = hs[c].min_chunk;
+        }
+        trace->tasks_small = Ts;
         float ms = 0.f;
         TC_CUDA_TRY(cudaEventElapsedTime(&ms, ev[0], ev[1]));
         trace->prefix_ms = ms;
         TC_CUDA_TRY(cudaEventElapsedTime(&ms, ev[1], ev[2]));
-        trace->kernel_ms = ms;
+        trace->kernel_small_ms = ms;
+        TC_CUDA_TRY(cudaEventElapsedTime(&ms, ev[2], ev[3]));
+        trace->kernel_big_ms = ms;
         for (auto& e : ev) cudaEventDestroy(e);
     }
     return TC_OK;

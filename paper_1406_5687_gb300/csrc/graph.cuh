@@ -23,7 +23,7 @@ struct Sched {
     unsigned long long min_chunk;
     unsigned long long head;
     unsigned long long n_chunks;
-    unsigned long long total;
+    unsigned long long base;  // exclusive prefix at the class's first task
 };
 
 // Device counters written by the build kernels.
@@ -34,6 +34,7 @@ struct BuildCounters {
     unsigned long long sum_dhat_v;
     unsigned long long sum_dhat_u;
     unsigned long long sum_stream;
+    unsigned long long tasks_small;
     long long bad_index;
     int max_degree;
     int max_dhat;
@@ -46,7 +47,7 @@ struct CountWork {
     uint64_t* scan_scr = nullptr;
     int64_t scan_words = 0;
     uint64_t* fcost = nullptr;    // n, per-vertex cost models only
-    Sched* sched = nullptr;
+    Sched* sched = nullptr;       // two: the small and the big class
     unsigned long long* result = nullptr;  // device copy of the last total
 };
 
@@ -59,6 +60,7 @@ struct tc_graph {
     int32_t n = 0;
     int id_bits = 1;
     int64_t m_in = 0, self_loops = 0, duplicates = 0, m_hat = 0, tasks = 0, bad_index = -1;
+    int64_t tasks_small = 0;       // tasks [0, tasks_small) have owners with at most opt.small_max entries
     int32_t max_degree = 0, max_dhat = 0;
     uint64_t sum_dhat_v = 0, sum_dhat_u = 0, sum_stream = 0;
     // device arrays owned by the handle
@@ -91,5 +93,12 @@ tc_status build_graph(tc_graph* g, const int32_t* src_d, const int32_t* dst_d, i
                       cudaStream_t s);
 
 tc_status check_options(const tc_options& o);
+
+// Slots of one small-class warp table: load at most 1/8 for lists of up to small_max entries.
+inline int small_table_slots(int small_max) {
+    int p = 4;
+    while (p < small_max) p <<= 1;
+    return 8 * p;
+}
 
 }  // namespace tcg

@@ -38,12 +38,14 @@ def test_host_only_calls():
     assert lib.tc_status_str(2).startswith(b"vertex id")
     assert b"sm_103a" in lib.tc_version()
     o = _lib.default_options()
-    assert (o.piece, o.warps_per_block, o.static_percent, o.cost_model) == (1024, 8, 50, 0)
+    assert (o.piece, o.warps_per_block, o.big_warps, o.small_max, o.static_percent, o.cost_model) == \
+        (2048, 8, 16, 64, 50, 0)
     # argument checks that return before touching a device
     h = ctypes.c_void_p()
     assert lib.tc_build(None, None, -1, 10, None, None, ctypes.byref(h)) == _lib.TC_ERR_INVALID_ARG
     assert lib.tc_build(None, None, 5, 10, None, None, ctypes.byref(h)) == _lib.TC_ERR_INVALID_ARG
-    bad = _lib.default_options(piece=1000)
-    assert lib.tc_build(None, None, 0, 10, ctypes.byref(bad), None, ctypes.byref(h)) == _lib.TC_ERR_INVALID_ARG
+    for bad in (_lib.default_options(piece=1000), _lib.default_options(small_max=100),
+                _lib.default_options(big_warps=32), _lib.default_options(static_percent=101)):
+        assert lib.tc_build(None, None, 0, 10, ctypes.byref(bad), None, ctypes.byref(h)) == _lib.TC_ERR_INVALID_ARG
     assert lib.tc_count(None, None, None) == _lib.TC_ERR_INVALID_ARG
     lib.tc_free(None)

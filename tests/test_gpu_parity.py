@@ -87,14 +87,32 @@ def test_csr_matches_oracle(built, name):
     assert info["sum_dhat_u"] == int(dh[csr.cols].sum())
 
 
+SMALL_MAX = 64  # the default build option
+
+
 @pytest.mark.parametrize("name", list(GRAPHS))
 def test_tasks_match_oracle(built, name):
     g, csr = built[name]
     _, _, _, tasks = g.csr()
     t = tasks.cpu().numpy().astype(np.int64)
-    o, p = oracle.tasks(csr)
+    o, p, ns = oracle.tasks(csr, small_max=SMALL_MAX, with_split=True)
+    assert g.info()["tasks_small"] == ns
     assert np.array_equal(t[:, 0], o) and np.array_equal(t[:, 1], p)
     assert np.array_equal(t[:, 2], csr.off[p]) and np.array_equal(t[:, 3], np.diff(csr.off)[p])
+
+
+@pytest.mark.parametrize("small_max", [0, 16, 256])
+def test_small_max_build_option(small_max):
+    for name in ("cl_200k", "cl_dense", "wheel_1000"):
+        n, s, d = GRAPHS[name]
+        csr = oracle_csr(n, s, d)
+        with tc.Graph.build(s, d, n, tc.default_options(small_max=small_max)) as g:
+            _, _, _, tasks = g.csr()
+            t = tasks.cpu().numpy().astype(np.int64)
+            o, p, ns = oracle.tasks(csr, small_max=small_max, with_split=True)
+            assert g.info()["tasks_small"] == ns
+            assert np.array_equal(t[:, 0], o) and np.array_equal(t[:, 1], p)
+            assert g.count() == oracle.count(csr)
 
 
 @pytest.mark.parametrize("name", list(GRAPHS))
@@ -127,36 +145,52 @@ def test_vertex_cost(built, name, fn):
     assert np.array_equal(f, oracle.vertex_cost(csr, fn))
 
 
+def _sorted_rows(x):
+    return x[np.lexsort(tuple(x[:, k] for k in range(x.shape[1] - 1, -1, -1)))]
+
+
 @pytest.mark.parametrize("name", ["er_20k", "cl_200k", "cl_dense", "book_5000"])
-@pytest.mark.parametrize("model,piece", [(tc.TC_COST_EDGE, 1024), (tc.TC_COST_EDGE, 128), (tc.TC_COST_MERGE, 512),
-                                         (tc.TC_COST_DEGREE, 256), (tc.TC_COST_PATRIC, 1024),
-                                         (tc.TC_COST_NEW, 2048), (tc.TC_COST_ONE, 1024)])
+@pytest.mark.parametrize("model,piece", [(tc.TC_COST_EDGE, 2048), (tc.TC_COST_EDGE, 256), (tc.TC_COST_MERGE, 512),
+                                         (tc.TC_COST_DEGREE, 1024), (tc.TC_COST_PATRIC, 2048),
+                                         (tc.TC_COST_NEW, 4096), (tc.TC_COST_ONE, 2048)])
 def test_schedule_matches_oracle(built, name, model, piece):
-    """The chunks the workers took are exactly Eq. 1 + Eq. 2 over the oracle's task costs."""
+    """Per class, the chunks the workers took are exactly Eq. 1 + Eq. 2 over the oracle's task costs."""
     g, csr = built[name]
-    wpb = 16 if piece <= 1024 else 4
-    opt = tc.default_options(cost_model=model, piece=piece, warps_per_block=wpb)
+    big_warps = 16 if piece <= 2048 else 8
+    opt = tc.default_options(cost_model=model, piece=piece, warps_per_block=16, big_warps=big_warps)
     T, meta, chunks, busy = g.count_ex(opt, trace_cap=1 << 20, busy=True)
     assert T == oracle.count(csr)
-    o, p = oracle.tasks(csr)
+    o, p, ns = oracle.tasks(csr, small_max=SMALL_MAX, with_split=True)
+    assert meta["tasks_small"] == ns
     if model == tc.TC_COST_EDGE:
-        cost = oracle.task_costs(csr, o, p, oracle.MODEL_EDGE, piece=piece, c_task=4, c_owner=32)
+        cost = oracle.task_costs(csr, o, p, oracle.MODEL_EDGE, piece=piece, c_task=4, c_owner=32,
+                                 small_max=SMALL_MAX)
     elif model == tc.TC_COST_MERGE:
         cost = oracle.task_costs(csr, o, p, oracle.MODEL_MERGE)
     else:
         cost = oracle.task_costs(csr, o, p, oracle.MODEL_VERTEX, fn=model - tc.TC_COST_ONE)
-    assert meta["total_cost"] == int(cost.sum())
-    cb, tb = oracle.schedule(cost, meta["n_workers"], meta["min_chunk"])
-    want = np.stack([cb[:-1], cb[1:], tb[:-1], tb[1:]], axis=1).astype(np.int64)
     got = chunks.cpu().numpy()
-    assert meta["n_chunks"] == len(want)
-    W = meta["n_workers"]
-    # static chunks are recorded by worker; dynamic ones in pop order -- compare as sets ordered by cost
-    got = got[np.lexsort((got[:, 3], got[:, 2], got[:, 1], got[:, 0]))]
-    want = want[np.lexsort((want[:, 3], want[:, 2], want[:, 1], want[:, 0]))]
-    assert np.array_equal(got, want)
+    n_want = 0
+    for cls, (lo, hi) in enumerate(((0, ns), (ns, len(o)))):
+        c = cost[lo:hi]
+        assert meta["total_cost"][cls] == int(c.sum())
+        mine = got[got[:, 0] == cls][:, 1:]
+        if hi == lo:
+            assert len(mine) == 0  # an empty class launches no kernel
+            continue
+        cb, tb = oracle.schedule(c, meta["n_workers"][cls], meta["min_chunk"][cls])
+        want = np.stack([cb[:-1], cb[1:], tb[:-1] + lo, tb[1:] + lo], axis=1).astype(np.int64)
+        n_want += len(want)
+        # static chunks are recorded per worker, dynamic ones in pop order: compare as sorted rows
+        assert np.array_equal(_sorted_rows(mine), _sorted_rows(want))
+    assert meta["n_chunks"] == n_want == len(got)
     b = busy.cpu().numpy()
-    assert b.shape[0] == W and int(b[:, 1].sum()) == len(want)
+    W = meta["n_workers"]
+    assert b.shape[0] == W[0] + W[1]
+    if ns > 0:
+        assert int(b[:W[0], 1].sum()) == int((got[:, 0] == 0).sum())
+    if len(o) > ns:
+        assert int(b[W[0]:, 1].sum()) == int((got[:, 0] == 1).sum())
 
 
 @pytest.mark.parametrize("static_percent", [0, 25, 50, 100])
@@ -168,12 +202,14 @@ def test_schedule_parameters_keep_the_count(built, static_percent, min_chunk):
     assert T == oracle.count(csr)
 
 
-@pytest.mark.parametrize("wpb,piece,bps", [(1, 128, 0), (4, 512, 2), (16, 1024, 1), (4, 2048, 0), (8, 256, 3)])
-def test_launch_shapes_keep_the_count(built, wpb, piece, bps):
-    g, csr = built["cl_dense"]
-    opt = tc.default_options(warps_per_block=wpb, piece=piece, blocks_per_sm=bps)
-    T, *_ = g.count_ex(opt)
-    assert T == oracle.count(csr)
+@pytest.mark.parametrize("wpb,piece,bps,bw", [(1, 256, 0, 4), (4, 512, 2, 8), (16, 1024, 1, 16), (4, 2048, 0, 16),
+                                           (8, 4096, 1, 8), (2, 256, 3, 16)])
+def test_launch_shapes_keep_the_count(built, wpb, piece, bps, bw):
+    for name in ("cl_dense", "cl_200k", "ba_30k"):
+        g, csr = built[name]
+        opt = tc.default_options(warps_per_block=wpb, piece=piece, blocks_per_sm=bps, big_warps=bw)
+        T, *_ = g.count_ex(opt)
+        assert T == oracle.count(csr)
 
 
 def test_device_input_and_dirty_input():

@@ -164,3 +164,31 @@ def test_vertex_model_chunks_never_split_an_owner():
         for t in tb[1:-1]:
             if 0 < t < len(owner):
                 assert owner[t] != owner[t - 1]
+
+
+def test_task_classes_split_by_owner_list_length():
+    n, s, d, csr = _csr(8, 800)
+    dh = np.diff(csr.off)
+    o_all, p_all = oracle.tasks(csr)
+    for k in (0, 3, 8, 20, 10**9):
+        o, p, ns = oracle.tasks(csr, small_max=k, with_split=True)
+        assert set(zip(o.tolist(), p.tolist())) == set(zip(o_all.tolist(), p_all.tolist()))
+        assert np.all(dh[o[:ns]] <= k) and np.all(dh[o[ns:]] > k)
+        for lo, hi in ((0, ns), (ns, len(o))):
+            key = o[lo:hi].astype(np.int64) * n + p[lo:hi]
+            assert np.all(np.diff(key) > 0)
+
+
+def test_task_costs_with_classes_worked_example():
+    """W_6 again, with small_max = 2: owner 1 (list of 3) is big, owners 2, 3, 4 are small.
+    Order: small (2,3) (3,4) (4,5), then big (1,2) (1,5).
+    EDGE, piece = 2, c_task = 4, c_owner = 32 (small owners take one piece):
+      (2,3): 1*(2+4) + 2+32 = 40; (3,4): 40; (4,5): 1*(1+4) + 34 = 39;
+      (1,2): 2*(2+4) = 12; (1,5): 2*(1+4) + 3+32 = 45."""
+    n, s, d = F.wheel(6)
+    csr = oracle.oriented_csr(oracle.simple_graph(n, s, d))
+    o, p, ns = oracle.tasks(csr, small_max=2, with_split=True)
+    assert ns == 3
+    assert list(zip(o.tolist(), p.tolist())) == [(2, 3), (3, 4), (4, 5), (1, 2), (1, 5)]
+    c = oracle.task_costs(csr, o, p, oracle.MODEL_EDGE, piece=2, c_task=4, c_owner=32, small_max=2)
+    assert list(c) == [40, 40, 39, 12, 45]
