@@ -94,16 +94,16 @@ typedef void (*tc_release_fn)(void* ctx, void* ptr, tc_stream_t stream);
 
 /*
  * Tasks fall in two classes by the length of the owner's list.  Small owners (at most
- * small_max entries) are counted by one warp each, with a per-warp hash table;
- * big owners by a whole block, whose warps share one table of 8 * piece slots
- * (lists longer than `piece` are staged in pieces, each partner list streamed once
- * per piece).
+ * small_max entries) are counted with per-warp hash tables, several owners at a time;
+ * big owners one at a time by a whole block, whose warps share one table of 8 * piece
+ * slots (lists longer than `piece` are staged in pieces, each partner list streamed
+ * once per piece).  In both classes one block is one worker of the schedule.
  */
 typedef struct tc_options {
     int32_t input_policy;      /* tc_input_policy */
     int32_t cost_model;        /* tc_cost_model */
     int32_t piece;             /* big owners: list entries staged per block table: 256..4096, power of 2 (default 2048) */
-    int32_t warps_per_block;   /* small-class kernel: warps (workers) per block: 1..16, power of 2 (default 8) */
+    int32_t warps_per_block;   /* small-class kernel: warps per block: 1..16, power of 2 (default 16) */
     int32_t blocks_per_sm;     /* cap on resident blocks per SM of both count kernels (0 = as many as fit) */
     int32_t big_warps;         /* big-class kernel: warps per block (one worker): 4, 8 or 16 (default 16) */
     int32_t small_max;         /* build option: owners with at most this many list entries are small:
@@ -241,9 +241,9 @@ tc_status tc_vertex_cost(tc_graph_t g, int32_t fn, tc_stream_t stream, uint64_t*
  *                      task indices into the whole task array, in no particular
  *                      order; records beyond cap are dropped;
  *              workers_busy device, 2*(n_workers[0] + n_workers[1]) uint64 or
- *                      NULL: per worker (small-class warps first, then big-class
- *                      blocks), (clock64 cycles spent on tasks, chunks taken) --
- *                      the per-worker idle time of Sec. V-E;
+ *                      NULL: per worker (a worker is one block; small-class blocks
+ *                      first, then big-class blocks), (clock64 cycles spent on
+ *                      tasks, chunks taken) -- the per-worker idle time of Sec. V-E;
  *            and on return: n_chunks (records produced), and per class c:
  *            n_workers[c] (W), total_cost[c] (C), min_chunk[c] (the Eq. 2 floor
  *            used); tasks_small; the CUDA-event times of the cost prefix and

@@ -74,6 +74,7 @@ static void free_graph(tc_graph* g) {
     put(g->off, ((size_t)g->n + 1) * 8);
     put(g->cols, (size_t)(g->m_hat > 0 ? g->m_hat : 1) * 4);
     put(g->trec, (size_t)(g->tasks > 0 ? g->tasks : 1) * sizeof(TaskRec));
+    put(g->own_first, (size_t)g->own_first_cap * 4);
     put(g->work.prefix, (size_t)(g->tasks + 1) * 8);
     put(g->work.scan_scr, (size_t)g->work.scan_words * 8);
     put(g->work.fcost, (size_t)(g->n > 0 ? g->n : 1) * 8);
@@ -123,7 +124,7 @@ void tc_options_default(tc_options* o) {
     o->input_policy = TC_INPUT_SANITIZE;
     o->cost_model = TC_COST_EDGE;
     o->piece = 2048;
-    o->warps_per_block = 8;
+    o->warps_per_block = 16;
     o->big_warps = 16;
     o->small_max = 64;
     o->blocks_per_sm = 0;

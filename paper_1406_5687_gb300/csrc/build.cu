@@ -241,6 +241,20 @@ __global__ void k_task_keys(const uint64_t* __restrict__ okeys, const int32_t* _
     }
 }
 
+// First task of each big-class owner: t in [Ts, T) where the owner changes.
+struct OwnerStartPred {
+    const TaskRec* rec;
+    int64_t Ts;
+    __device__ bool operator()(int64_t i) const {
+        const int64_t t = Ts + i;
+        return t == Ts || rec[t].owner != rec[t - 1].owner;
+    }
+};
+struct OwnerStartVal {
+    int64_t Ts;
+    __device__ uint32_t operator()(int64_t i) const { return (uint32_t)(Ts + i); }
+};
+
 __global__ void k_task_records(const uint64_t* __restrict__ tkeys, int64_t T, int b, const int64_t* __restrict__ off,
                                TaskRec* __restrict__ rec) {
     const uint64_t mask = (1ull << b) - 1;
@@ -388,6 +402,20 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
 
     g->tasks = T;
     g->tasks_small = (int64_t)hc.tasks_small;
+    // first task of every big owner, plus T at the end
+    {
+        const int64_t nb = T - g->tasks_small;
+        DevBuf<uint32_t> of;
+        TC_TRY(of.alloc(al, (size_t)(nb + 1), s));
+        uint64_t k = 0;
+        TC_TRY(compact(OwnerStartPred{rec.ptr, g->tasks_small}, OwnerStartVal{g->tasks_small}, nb, of.ptr, al, s, &k));
+        const uint32_t endv = (uint32_t)T;
+        TC_CUDA_TRY(cudaMemcpyAsync(of.ptr + k, &endv, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        TC_CUDA_TRY(cudaStreamSynchronize(s));
+        g->owners_big = (int64_t)k;
+        g->own_first_cap = (int64_t)(nb + 1);
+        g->own_first = of.detach();
+    }
     g->max_degree = hc.max_degree;
     g->max_dhat = hc.max_dhat;
     g->sum_dhat_v = hc.sum_dhat_v;
@@ -400,7 +428,8 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     g->trec = rec.detach();
     g->bytes = (int64_t)align_up((size_t)(n > 0 ? n : 1) * 4, 256) + (int64_t)align_up(((size_t)n + 1) * 8, 256) +
                (int64_t)align_up((size_t)(mh > 0 ? mh : 1) * 4, 256) +
-               (int64_t)align_up((size_t)(T > 0 ? T : 1) * sizeof(TaskRec), 256);
+               (int64_t)align_up((size_t)(T > 0 ? T : 1) * sizeof(TaskRec), 256) +
+               (int64_t)align_up((size_t)g->own_first_cap * 4, 256);
     TC_CUDA_TRY(cudaStreamSynchronize(s));
     return TC_OK;
 }

@@ -8,14 +8,16 @@
 // streamed through it.  Each edge thus costs min(|N_v|, |N_u|) streamed entries instead of
 // the |N_v| + |N_u| of a merge (Sec. III-A).
 //
-// Two task classes, two kernels.  Owners with at most small_max entries are counted by one
-// warp each (a table per warp); longer owners by a whole block whose warps share one table
-// and pull batches of 32 tasks from a block counter.  Inside a batch, partner lists of 32
-// or more entries are streamed by the whole warp one list at a time; shorter ones are
-// concatenated and spread over the lanes.
+// Two task classes, two kernels.  Owners with at most small_max entries: each warp takes
+// windows of up to 32 consecutive tasks and stages the lists of all the window's owners
+// at once, each in its own region of the warp's table.  Longer owners: a block stages a
+// window of consecutive owners into regions of one shared table and its warps pull
+// batches of 32 of the window's tasks from a block counter.
+// Inside a batch, partner lists of 32 or more entries are streamed by the whole warp one
+// list at a time; shorter ones are concatenated and spread over the lanes.
 //
-// Schedule (Sec. V-B), per class.  The persistent grid has W workers (warps for the small
-// class, blocks for the big one).  Task costs are prefix-summed (uint64).  The first
+// Schedule (Sec. V-B), per class.  The persistent grid has W workers, one per block (the
+// warps of a block share its chunk).  Task costs are prefix-summed (uint64).  The first
 // H = floor(C * static_percent / 100) cost units (Eq. 1, default one half) are split into W
 // equal initial chunks, one per worker, taken without coordination; the rest is handed out
 // by a compare-and-swap on a device head, each pop taking max(min_chunk,
@@ -56,6 +58,8 @@ struct CountArgs {
     long long busy_offset;
     DevStatus* status;
     long long retry_limit;
+    const uint32_t* own_first;  // big class: first task of each owner, then T
+    long long n_owners;         // big class: owners
 };
 
 // First index q in [lo, hi] with pred(q), for pred false..false true..true and pred(hi) true.
@@ -167,10 +171,24 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
     return pos;
 }
 
-// One warp counts a batch of nb <= 32 tasks of `owner` (lane i holds task i's record)
-// against the owner's staged table.
+// A table region packed in 32 bits: slot offset in the low 16 bits, log2(slots) above.
+__device__ __forceinline__ uint32_t pack_region(uint32_t base, uint32_t cap) {
+    return base | ((uint32_t)(__ffs(cap) - 1) << 16);
+}
+
+__device__ __forceinline__ HashView region_view(uint32_t* tbl, uint32_t reg) {
+    const uint32_t lg = reg >> 16;
+    HashView hv;
+    hv.tbl = tbl + (reg & 0xFFFFu);
+    hv.cmask = (1u << lg) - 1u;
+    hv.shift = 32 - (int)lg;
+    return hv;
+}
+
+// One warp counts a batch of nb <= 32 tasks (lane i holds task i's record and, in
+// `reg`, the table region of that task's owner) against the staged owner lists.
 template <bool EXTRA>
-__device__ void warp_batch(const CountArgs& a, const TaskRec& r, int nb, uint32_t owner, const HashView& hv,
+__device__ void warp_batch(const CountArgs& a, const TaskRec& r, int nb, uint32_t* __restrict__ tbl, uint32_t reg,
                            int lane, unsigned long long& acc) {
     const uint32_t len = lane < nb ? r.plen : 0u;
     // partner lists of 32 or more entries: the whole warp streams one list at a time
@@ -180,8 +198,12 @@ __device__ void warp_batch(const CountArgs& a, const TaskRec& r, int nb, uint32_
         longm &= longm - 1;
         const uint32_t s = __shfl_sync(kFull, r.pstart, j);
         const uint32_t L = __shfl_sync(kFull, len, j);
-        uint32_t pj = 0;
-        if (EXTRA) pj = __shfl_sync(kFull, r.partner, j);
+        const HashView hv = region_view(tbl, __shfl_sync(kFull, reg, j));
+        uint32_t pj = 0, oj = 0;
+        if (EXTRA) {
+            pj = __shfl_sync(kFull, r.partner, j);
+            oj = __shfl_sync(kFull, r.owner, j);
+        }
         const int32_t* __restrict__ lst = a.cols + s;
         for (uint32_t base = 0; base < L; base += 32u * kUnroll) {
             uint32_t wv[kUnroll];
@@ -196,7 +218,7 @@ __device__ void warp_batch(const CountArgs& a, const TaskRec& r, int nb, uint32_
             for (int u = 0; u < kUnroll; ++u) {
                 const bool hit = ok[u] && hash_probe(hv, wv[u]);
                 acc += hit ? 1ull : 0ull;
-                if (EXTRA && hit) on_hit<EXTRA>(a, owner, pj, wv[u]);
+                if (EXTRA && hit) on_hit<EXTRA>(a, oj, pj, wv[u]);
             }
         }
     }
@@ -209,15 +231,19 @@ __device__ void warp_batch(const CountArgs& a, const TaskRec& r, int nb, uint32_
     const int src = lane < ns ? nth_set_bit(smask, lane) : 0;
     const uint32_t g_len = __shfl_sync(kFull, short_len, src);
     const uint32_t g_start = __shfl_sync(kFull, r.pstart, src);
-    uint32_t g_partner = 0;
-    if (EXTRA) g_partner = __shfl_sync(kFull, r.partner, src);
+    const uint32_t g_reg = __shfl_sync(kFull, reg, src);
+    uint32_t g_partner = 0, g_owner = 0;
+    if (EXTRA) {
+        g_partner = __shfl_sync(kFull, r.partner, src);
+        g_owner = __shfl_sync(kFull, r.owner, src);
+    }
     const uint32_t slen = lane < ns ? g_len : 0u;
     const uint32_t incl = warp_inclusive_scan(slen, lane);
     const uint32_t excl = incl - slen;
     const uint32_t tot = __shfl_sync(kFull, incl, 31);
-    uint32_t before = 0;  // tasks whose entries start before the current window
+    uint32_t before = 0;  // gathered tasks whose entries start before the current window
     for (uint32_t base = 0; base < tot; base += 32u * kUnroll) {
-        uint32_t wv[kUnroll];
+        uint32_t wv[kUnroll], rg[kUnroll];
         bool ok[kUnroll];
         int qj[kUnroll];
 #pragma unroll
@@ -231,6 +257,7 @@ __device__ void warp_batch(const CountArgs& a, const TaskRec& r, int nb, uint32_
             const int q = ((int)(before + __popc(starts & lanemask_le())) - 1) & 31;
             const uint32_t sj = __shfl_sync(kFull, g_start, q);
             const uint32_t ej = __shfl_sync(kFull, excl, q);
+            rg[u] = __shfl_sync(kFull, g_reg, q);
             const uint32_t g = wb + lane;
             ok[u] = g < tot;
             wv[u] = ok[u] ? (uint32_t)__ldg(&a.cols[(long long)sj + (g - ej)]) : 0u;
@@ -239,11 +266,12 @@ __device__ void warp_batch(const CountArgs& a, const TaskRec& r, int nb, uint32_
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const bool hit = ok[u] && hash_probe(hv, wv[u]);
+            const bool hit = ok[u] && hash_probe(region_view(tbl, rg[u]), wv[u]);
             acc += hit ? 1ull : 0ull;
             if (EXTRA) {
                 const uint32_t pj = __shfl_sync(kFull, g_partner, qj[u]);
-                if (hit) on_hit<EXTRA>(a, owner, pj, wv[u]);
+                const uint32_t oj = __shfl_sync(kFull, g_owner, qj[u]);
+                if (hit) on_hit<EXTRA>(a, oj, pj, wv[u]);
             }
         }
     }
@@ -283,155 +311,246 @@ __device__ __forceinline__ void trace_chunk(const CountArgs& a, unsigned long lo
 
 // ------------------------------------------------------------------ small owners: one warp each
 
+// A warp takes windows of up to 32 consecutive tasks.  The distinct owners of a window get
+// separate regions of the warp's table (each sized for a load of at most 1/8); their lists
+// are staged together, then all the window's tasks are counted.  One chain of dependent
+// loads per window instead of one per owner.
 template <bool EXTRA>
 __device__ void process_small(const CountArgs& a, long long t0, long long t1, uint32_t* __restrict__ tbl, int lane,
                               unsigned long long& acc) {
+    const uint32_t slots = (uint32_t)a.table_slots;
     long long t = t0;
     while (t < t1) {
-        const uint32_t owner = a.tasks[t].owner;
-        const long long obase = a.off[owner];
-        const uint32_t olen = (uint32_t)(a.off[owner + 1] - obase);
-        uint32_t cap = 32;
-        while (cap < 8 * olen) cap <<= 1;
-        const HashView hv = make_view(tbl, cap);
-        for (uint32_t i = lane; i < cap; i += 32) tbl[i] = kEmpty;
+        const long long j = t + lane;
+        const bool in = j < t1;
+        TaskRec r = {0u, 0u, 0u, 0u};
+        if (in) r = a.tasks[j];
+        const uint32_t prev = __shfl_up_sync(kFull, r.owner, 1);
+        const bool lead = in && (lane == 0 || r.owner != prev);  // first task of an owner in the window
+        long long ob = 0;
+        uint32_t ol = 0, cap = 0;
+        if (lead) {
+            ob = a.off[r.owner];
+            ol = (uint32_t)(a.off[r.owner + 1] - ob);
+            cap = 32;
+            while (cap < 8 * ol) cap <<= 1;
+        }
+        const uint32_t cend = warp_inclusive_scan(cap, lane);  // end of each leader's region
+        const unsigned lead_m = __ballot_sync(kFull, lead);
+        const unsigned fit_m = __ballot_sync(kFull, lead && cend <= slots);
+        // the window stops before the first owner whose region does not fit (lane 0's always does)
+        const unsigned over = lead_m & ~fit_m;
+        const int nt = over ? (__ffs(over) - 1) : __popc(__ballot_sync(kFull, in));
+        const unsigned kept = fit_m & (nt >= 32 ? kFull : ((1u << nt) - 1u));
+        // each task's region is its leader's
+        const int leader = 31 - __clz(lead_m & lanemask_le());
+        const uint32_t my_reg = lead ? pack_region(cend - cap, cap) : 0u;
+        const uint32_t reg = __shfl_sync(kFull, my_reg, leader);
+        const uint32_t used = __shfl_sync(kFull, cend, 31 - __clz(kept));
+        for (uint32_t i = lane; i < used; i += 32) tbl[i] = kEmpty;
         __syncwarp();
-        for (uint32_t i = lane; i < olen; i += 32) hash_insert(hv, (uint32_t)__ldg(&a.cols[obase + i]));
-        __syncwarp();
-        long long tt = t;
-        for (;;) {
-            const long long j = tt + lane;
-            TaskRec r = {0u, 0u, 0u, 0u};
-            bool valid = false;
-            if (j < t1) {
-                r = a.tasks[j];
-                valid = r.owner == owner;
-            }
-            const unsigned vb = __ballot_sync(kFull, valid);
-            const int nb = (vb == kFull) ? 32 : __ffs(~vb) - 1;  // leading run of this owner's tasks
-            warp_batch<EXTRA>(a, r, nb, owner, hv, lane, acc);
-            if (nb < 32) {
-                tt += nb;
-                break;
-            }
-            tt += 32;
+        // stage: gather the kept leaders into lanes 0..ng-1, spread their lists over the lanes
+        const int ng = __popc(kept);
+        const int src = lane < ng ? nth_set_bit(kept, lane) : 0;
+        const long long s_ob = __shfl_sync(kFull, ob, src);
+        const uint32_t s_len0 = __shfl_sync(kFull, ol, src);
+        const uint32_t s_reg = __shfl_sync(kFull, my_reg, src);
+        const uint32_t s_len = lane < ng ? s_len0 : 0u;
+        const uint32_t incl = warp_inclusive_scan(s_len, lane);
+        const uint32_t excl = incl - s_len;
+        const uint32_t tot = __shfl_sync(kFull, incl, 31);
+        uint32_t before = 0;
+        for (uint32_t base = 0; base < tot; base += 32u) {
+            const uint32_t rel = excl - base;
+            const uint32_t bit = (s_len != 0u && rel < 32u) ? (1u << rel) : 0u;
+            const uint32_t starts = __reduce_or_sync(kFull, bit);
+            const int q = ((int)(before + __popc(starts & lanemask_le())) - 1) & 31;
+            const long long obq = __shfl_sync(kFull, s_ob, q);
+            const uint32_t eq = __shfl_sync(kFull, excl, q);
+            const uint32_t rq = __shfl_sync(kFull, s_reg, q);
+            const uint32_t g = base + lane;
+            if (g < tot) hash_insert(region_view(tbl, rq), (uint32_t)__ldg(&a.cols[obq + (g - eq)]));
+            before += __popc(starts);
         }
         __syncwarp();
-        t = tt;
+        warp_batch<EXTRA>(a, r, nt, tbl, reg, lane, acc);
+        __syncwarp();
+        t += nt;
     }
 }
 
+// The warps of a block pull 32-task slices of the block's chunk [t0, t1) from a shared
+// counter and count each slice with process_small.
 template <bool EXTRA>
-__global__ void __launch_bounds__(512) k_count_small(CountArgs a) {
-    extern __shared__ uint32_t smem_tbl[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const long long wid = (long long)blockIdx.x * a.warps_per_block + wib;
-    uint32_t* tbl = smem_tbl + (size_t)wib * a.table_slots;
-    const unsigned long long C = a.sched->C, H = a.sched->H, minc = a.sched->min_chunk, base = a.sched->base;
-    const unsigned long long W = (unsigned long long)a.W;
-    unsigned long long acc = 0;
-    long long busy = 0, nch = 0;
-    if (wid < a.W) {
-        // Eq. 1: the initial share split into W parts of equal cost
-        const unsigned long long q = H / W, r = H % W, w0 = (unsigned long long)wid;
-        const unsigned long long lo = w0 * q + (w0 < r ? w0 : r);
-        const unsigned long long hi = (w0 + 1) * q + (w0 + 1 < r ? w0 + 1 : r);
-        long long t0 = wid == 0 ? a.t_begin : class_bound(a, lo, C, base, lane);
-        long long t1 = class_bound(a, hi, C, base, lane);
-        if (lane == 0) trace_chunk(a, lo, hi, t0, t1);
-        long long c0 = clock64();
-        process_small<EXTRA>(a, t0, t1, tbl, lane, acc);
-        busy += clock64() - c0;
-        ++nch;
-        // Eq. 2: guided chunks of the remaining cost
-        for (;;) {
-            unsigned long long c = 0, e = 0;
-            int got = 0;
-            if (lane == 0) got = pop_chunk(a, C, minc, c, e);
-            got = __shfl_sync(kFull, got, 0);
-            if (!got) break;
-            c = __shfl_sync(kFull, c, 0);
-            e = __shfl_sync(kFull, e, 0);
-            t0 = class_bound(a, c, C, base, lane);
-            t1 = class_bound(a, e, C, base, lane);
-            if (lane == 0) trace_chunk(a, c, e, t0, t1);
-            c0 = clock64();
-            process_small<EXTRA>(a, t0, t1, tbl, lane, acc);
-            busy += clock64() - c0;
-            ++nch;
-        }
+__device__ void process_small_block(const CountArgs& a, long long t0, long long t1, uint32_t* __restrict__ tbl,
+                                    unsigned* s_claim, int lane, unsigned long long& acc) {
+    if (threadIdx.x == 0) *s_claim = 0u;
+    __syncthreads();
+    for (;;) {
+        unsigned o = 0;
+        if (lane == 0) o = atomicAdd(s_claim, 32u);
+        o = __shfl_sync(kFull, o, 0);
+        const long long t = t0 + (long long)o;
+        if (t >= t1) break;
+        process_small<EXTRA>(a, t, t + 32 < t1 ? t + 32 : t1, tbl, lane, acc);
     }
-    acc = warp_sum(acc);
-    if (lane == 0) {
-        if (acc) atomicAdd(a.total, acc);
-        if (a.trace_busy && wid < a.W) {
-            a.trace_busy[2 * (a.busy_offset + wid)] = (uint64_t)busy;
-            a.trace_busy[2 * (a.busy_offset + wid) + 1] = (uint64_t)nch;
-        }
-    }
+    __syncthreads();
 }
 
 // ------------------------------------------------------------------ big owners: one block each
 
+constexpr int kWinOwners = 32;
+
+// A window of consecutive big owners staged together into regions of the block's table.
+struct BigWindow {
+    long long first[kWinOwners + 1];  // owner i's tasks of the window: [first[i], first[i + 1])
+    long long ob[kWinOwners];         // owner i's list: cols[ob[i], ob[i] + ol[i])
+    uint32_t ol[kWinOwners];
+    uint32_t reg[kWinOwners];         // owner i's table region
+    long long k;                      // owner index of the window's first owner
+    uint32_t used;                    // table slots in use
+    int nown;                         // owners in the window; 0: one owner needs several pieces
+};
+
+// Count the tasks [t, tend) of one owner whose list (cols[ob, ob + ol)) is longer than a
+// piece: the table holds one piece at a time and every partner list is streamed per piece.
+template <bool EXTRA>
+__device__ void big_owner_pieces(const CountArgs& a, long long t, long long tend, long long ob, uint32_t ol,
+                                 uint32_t* __restrict__ tbl, unsigned* s_next, int lane, unsigned long long& acc) {
+    for (uint32_t ps = 0; ps < ol; ps += (uint32_t)a.piece) {
+        const uint32_t pl = min((uint32_t)a.piece, ol - ps);
+        uint32_t cap = 1024;
+        while (cap < 8 * pl) cap <<= 1;
+        const HashView hv = make_view(tbl, cap);
+        const uint32_t reg = pack_region(0u, cap);
+        for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) tbl[i] = kEmpty;
+        if (threadIdx.x == 0) *s_next = 0;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < pl; i += blockDim.x) hash_insert(hv, (uint32_t)__ldg(&a.cols[ob + ps + i]));
+        __syncthreads();
+        for (;;) {
+            unsigned b = 0;
+            if (lane == 0) b = atomicAdd(s_next, 1u);
+            b = __shfl_sync(kFull, b, 0);
+            const long long tb = t + (long long)b * 32;
+            if (tb >= tend) break;
+            const int nb = (int)(tend - tb < 32 ? tend - tb : 32);
+            TaskRec r = {0u, 0u, 0u, 0u};
+            if (lane < nb) r = a.tasks[tb + lane];
+            warp_batch<EXTRA>(a, r, nb, tbl, reg, lane, acc);
+        }
+        __syncthreads();
+    }
+}
+
+// Count the big-class tasks [t0, t1) (every thread of the block calls this).  Consecutive
+// owners are taken in windows: as many as fit the block table at a load of at most 1/8
+// each; their lists are staged together and the block's warps pull batches of 32 of the
+// window's tasks from a block counter, each task probing its own owner's region.
 template <bool EXTRA>
 __device__ void process_big(const CountArgs& a, long long t0, long long t1, uint32_t* __restrict__ tbl,
-                            long long* s_seg, unsigned* s_next, int lane, int warp, unsigned long long& acc) {
+                            BigWindow* w, unsigned* s_next, int lane, int warp, unsigned long long& acc) {
+    if (t0 >= t1) return;
+    const int nwarps = blockDim.x >> 5;
+    if (warp == 0) {
+        // owner of t0: the last owner whose first task is at or before t0
+        const uint32_t* __restrict__ of = a.own_first;
+        const long long K = a.n_owners;
+        const long long k = warp_first_true(0, K, [&](long long q) { return q >= K || (long long)of[q] > t0; }, lane) - 1;
+        if (lane == 0) w->k = k;
+    }
+    __syncthreads();
+    long long k = w->k;
     long long t = t0;
     while (t < t1) {
-        const uint32_t owner = a.tasks[t].owner;
         if (warp == 0) {
-            const TaskRec* __restrict__ tk = a.tasks;
-            const long long e =
-                warp_first_true(t + 1, t1, [&](long long q) { return q >= t1 || tk[q].owner != owner; }, lane);
-            if (lane == 0) *s_seg = e;
+            const long long kq = k + lane;
+            const bool exists = kq < a.n_owners && (long long)a.own_first[kq] < t1;
+            long long ob = 0, first = 0;
+            uint32_t ol = 0, cap = 0;
+            if (exists) {
+                first = (long long)a.own_first[kq];
+                const uint32_t owner = a.tasks[first].owner;
+                ob = a.off[owner];
+                ol = (uint32_t)(a.off[owner + 1] - ob);
+                cap = 1024;
+                while (cap < 8 * ol) cap <<= 1;
+            }
+            const uint32_t cend = warp_inclusive_scan(cap, lane);
+            const unsigned fit = __ballot_sync(kFull, exists && cend <= (uint32_t)a.table_slots);
+            const int nown = fit == kFull ? 32 : __ffs(~fit) - 1;  // leading run of owners that fit
+            const uint32_t used = __shfl_sync(kFull, cend, (nown - 1) & 31);
+            if (lane < (nown > 0 ? nown : 1)) {
+                w->first[lane] = lane == 0 ? t : first;
+                w->ob[lane] = ob;
+                w->ol[lane] = ol;
+                w->reg[lane] = pack_region(cend - cap, cap);
+            }
+            if (lane == 0) {
+                const long long nk = k + (nown > 0 ? nown : 1);
+                const long long nf = (long long)a.own_first[nk];  // own_first[n_owners] = T
+                w->first[nown > 0 ? nown : 1] = nf < t1 ? nf : t1;
+                w->nown = nown;
+                w->used = nown > 0 ? used : 0u;
+            }
         }
-        const long long obase = a.off[owner];
-        const uint32_t olen = (uint32_t)(a.off[owner + 1] - obase);
         __syncthreads();
-        const long long seg_end = *s_seg;
-        for (uint32_t ps = 0; ps < olen; ps += (uint32_t)a.piece) {
-            const uint32_t pl = min((uint32_t)a.piece, olen - ps);
-            uint32_t cap = 256;
-            while (cap < 8 * pl) cap <<= 1;
-            const HashView hv = make_view(tbl, cap);
-            for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) tbl[i] = kEmpty;
+        const int nown = w->nown;
+        const long long tend = w->first[nown > 0 ? nown : 1];
+        if (nown == 0) {
+            big_owner_pieces<EXTRA>(a, t, tend, w->ob[0], w->ol[0], tbl, s_next, lane, acc);
+        } else {
+            const uint32_t used = w->used;
+            for (uint32_t i = threadIdx.x; i < used; i += blockDim.x) tbl[i] = kEmpty;
             if (threadIdx.x == 0) *s_next = 0;
             __syncthreads();
-            for (uint32_t i = threadIdx.x; i < pl; i += blockDim.x)
-                hash_insert(hv, (uint32_t)__ldg(&a.cols[obase + ps + i]));
+            for (int i = warp; i < nown; i += nwarps) {
+                const HashView hv = region_view(tbl, w->reg[i]);
+                const long long ob = w->ob[i];
+                const uint32_t ol = w->ol[i];
+                for (uint32_t e = lane; e < ol; e += 32) hash_insert(hv, (uint32_t)__ldg(&a.cols[ob + e]));
+            }
             __syncthreads();
-            // the block's warps pull batches of 32 of the owner's tasks
             for (;;) {
                 unsigned b = 0;
                 if (lane == 0) b = atomicAdd(s_next, 1u);
                 b = __shfl_sync(kFull, b, 0);
                 const long long tb = t + (long long)b * 32;
-                if (tb >= seg_end) break;
-                const int nb = (int)(seg_end - tb < 32 ? seg_end - tb : 32);
+                if (tb >= tend) break;
+                const int nb = (int)(tend - tb < 32 ? tend - tb : 32);
                 TaskRec r = {0u, 0u, 0u, 0u};
-                if (lane < nb) r = a.tasks[tb + lane];
-                warp_batch<EXTRA>(a, r, nb, owner, hv, lane, acc);
+                uint32_t reg = 0u;
+                if (lane < nb) {
+                    const long long j = tb + lane;
+                    r = a.tasks[j];
+                    int lo = 0, hi = nown - 1;  // the last window owner whose tasks start at or before j
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (w->first[mid] <= j) lo = mid; else hi = mid - 1;
+                    }
+                    reg = w->reg[lo];
+                }
+                warp_batch<EXTRA>(a, r, nb, tbl, reg, lane, acc);
             }
             __syncthreads();
         }
-        t = seg_end;
+        t = tend;
+        k += nown > 0 ? nown : 1;
     }
 }
 
-template <bool EXTRA>
-__global__ void __launch_bounds__(512, 2) k_count_big(CountArgs a) {
-    extern __shared__ uint32_t smem_tbl[];
+// Scheduling loop of one block-wide worker (Sec. V-B): its Eq. 1 initial chunk, then Eq. 2
+// chunks popped by thread 0 until the class's cost is exhausted.  `process(t0, t1)` is
+// called by every thread of the block.
+template <class Process>
+__device__ __forceinline__ void block_worker(const CountArgs& a, Process process, int lane, int warp,
+                                             long long& busy, long long& nch) {
     __shared__ long long s_t[2];
     __shared__ unsigned long long s_c[2];
-    __shared__ long long s_seg;
-    __shared__ unsigned s_next;
     __shared__ int s_got;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long wid = blockIdx.x;
     const unsigned long long C = a.sched->C, H = a.sched->H, minc = a.sched->min_chunk, base = a.sched->base;
     const unsigned long long W = (unsigned long long)a.W;
-    unsigned long long acc = 0;
-    long long busy = 0, nch = 0;
     // Eq. 1: the initial share split into W parts of equal cost, one per block
     if (warp == 0) {
         const unsigned long long q = H / W, r = H % W, w0 = (unsigned long long)wid;
@@ -447,7 +566,7 @@ __global__ void __launch_bounds__(512, 2) k_count_big(CountArgs a) {
     }
     __syncthreads();
     long long c0 = clock64();
-    process_big<EXTRA>(a, s_t[0], s_t[1], smem_tbl, &s_seg, &s_next, lane, warp, acc);
+    process(s_t[0], s_t[1]);
     busy += clock64() - c0;
     ++nch;
     // Eq. 2: guided chunks of the remaining cost
@@ -472,16 +591,50 @@ __global__ void __launch_bounds__(512, 2) k_count_big(CountArgs a) {
         }
         __syncthreads();
         c0 = clock64();
-        process_big<EXTRA>(a, s_t[0], s_t[1], smem_tbl, &s_seg, &s_next, lane, warp, acc);
+        process(s_t[0], s_t[1]);
         busy += clock64() - c0;
         ++nch;
     }
+}
+
+template <bool EXTRA>
+__device__ __forceinline__ void worker_epilogue(const CountArgs& a, unsigned long long acc, int lane, long long busy,
+                                                long long nch) {
     acc = warp_sum(acc);
     if (lane == 0 && acc) atomicAdd(a.total, acc);
     if (threadIdx.x == 0 && a.trace_busy) {
-        a.trace_busy[2 * (a.busy_offset + wid)] = (uint64_t)busy;
-        a.trace_busy[2 * (a.busy_offset + wid) + 1] = (uint64_t)nch;
+        a.trace_busy[2 * (a.busy_offset + blockIdx.x)] = (uint64_t)busy;
+        a.trace_busy[2 * (a.busy_offset + blockIdx.x) + 1] = (uint64_t)nch;
     }
+}
+
+// Small owners: one worker per block, a table per warp.
+template <bool EXTRA>
+__global__ void __launch_bounds__(512, 2) k_count_small(CountArgs a) {
+    extern __shared__ uint32_t smem_tbl[];
+    __shared__ unsigned s_claim;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* tbl = smem_tbl + (size_t)warp * a.table_slots;
+    unsigned long long acc = 0;
+    long long busy = 0, nch = 0;
+    block_worker(a, [&](long long t0, long long t1) { process_small_block<EXTRA>(a, t0, t1, tbl, &s_claim, lane, acc); },
+                 lane, warp, busy, nch);
+    worker_epilogue<EXTRA>(a, acc, lane, busy, nch);
+}
+
+// Big owners: one worker per block, one table per block.
+template <bool EXTRA>
+__global__ void __launch_bounds__(512, 2) k_count_big(CountArgs a) {
+    extern __shared__ uint32_t smem_tbl[];
+    __shared__ BigWindow s_win;
+    __shared__ unsigned s_next;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long acc = 0;
+    long long busy = 0, nch = 0;
+    block_worker(a, [&](long long t0, long long t1) {
+        process_big<EXTRA>(a, t0, t1, smem_tbl, &s_win, &s_next, lane, warp, acc);
+    }, lane, warp, busy, nch);
+    worker_epilogue<EXTRA>(a, acc, lane, busy, nch);
 }
 
 // --------------------------------------------------------------------------- costs (a6)
@@ -630,7 +783,7 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     CountWork& w = g->work;
     const bool extra = t_v != nullptr || per_edge != nullptr;
     const long long T = g->tasks, Ts = g->tasks_small;
-    // small class: warps with their own tables
+    // small class: blocks whose warps each have a table
     const int wpb = opt.warps_per_block;
     const int slots_s = small_table_slots(g->opt.small_max);
     const size_t smem_s = (size_t)wpb * slots_s * sizeof(uint32_t);
@@ -646,7 +799,7 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
         TC_TRY(grid_for_kernel(k_count_small<false>, wpb * 32, smem_s, opt.blocks_per_sm, &blocks_s));
         TC_TRY(grid_for_kernel(k_count_big<false>, threads_b, smem_b, opt.blocks_per_sm, &blocks_b));
     }
-    const long long W_s = (long long)blocks_s * wpb, W_b = blocks_b;
+    const long long W_s = blocks_s, W_b = blocks_b;  // one worker per block in both classes
 
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     if (trace) {
@@ -684,6 +837,8 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     a.trace_busy = trace ? trace->workers_busy : nullptr;
     a.status = g->status;
     a.retry_limit = opt.retry_limit > 0 ? opt.retry_limit : (1ll << 24);
+    a.own_first = g->own_first;
+    a.n_owners = g->owners_big;
     // small class
     a.t_begin = 0;
     a.t_end = Ts;

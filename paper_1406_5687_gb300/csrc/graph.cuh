@@ -68,6 +68,8 @@ struct tc_graph {
     int64_t* off = nullptr;        // n + 1
     int32_t* cols = nullptr;       // m_hat
     tcg::TaskRec* trec = nullptr;  // tasks
+    uint32_t* own_first = nullptr; // first task of each big owner, then `tasks` (owners_big + 1 used)
+    int64_t owners_big = 0, own_first_cap = 0;
     tcg::DevStatus* status = nullptr;
     tcg::CountWork work;
     int64_t bytes = 0;             // device bytes held
@@ -94,11 +96,13 @@ tc_status build_graph(tc_graph* g, const int32_t* src_d, const int32_t* dst_d, i
 
 tc_status check_options(const tc_options& o);
 
-// Slots of one small-class warp table: load at most 1/8 for lists of up to small_max entries.
+// Slots of one small-class warp table: room for one owner of small_max entries at a load of
+// at most 1/8, and at least 1024 so that a window of tiny owners fits at once.  Region
+// offsets are packed in 16 bits, so at most 32768.
 inline int small_table_slots(int small_max) {
     int p = 4;
     while (p < small_max) p <<= 1;
-    return 8 * p;
+    return 8 * p > 1024 ? 8 * p : 1024;
 }
 
 }  // namespace tcg

@@ -39,7 +39,7 @@ def test_host_only_calls():
     assert b"sm_103a" in lib.tc_version()
     o = _lib.default_options()
     assert (o.piece, o.warps_per_block, o.big_warps, o.small_max, o.static_percent, o.cost_model) == \
-        (2048, 8, 16, 64, 50, 0)
+        (2048, 16, 16, 64, 50, 0)
     # argument checks that return before touching a device
     h = ctypes.c_void_p()
     assert lib.tc_build(None, None, -1, 10, None, None, ctypes.byref(h)) == _lib.TC_ERR_INVALID_ARG
