@@ -134,7 +134,8 @@ typedef struct tc_graph* tc_graph_t;
  * task array.
  *   src, dst  host or device, m int32 each: edge i is (src[i], dst[i]); never modified.
  *   m         number of input pairs (>= 0).
- *   n         number of vertices, 0 <= n < 2^31 - 1.
+ *   n         number of vertices, 0 <= n <= 2^30 (TC_ERR_UNSUPPORTED beyond);
+ *             at most 2^32 - 2 distinct edges.
  *   opt       NULL for defaults; copied into the handle.
  *   out       receives the handle; NULL on error.
  * Errors: TC_ERR_INVALID_ARG (NULL pointers with m > 0, negative sizes, bad
@@ -215,9 +216,9 @@ tc_status tc_graph_get_info(tc_graph_t g, tc_graph_info* info);
  *   deg   n int32          d_v
  *   off   n+1 int64        N+(v) = cols[off[v] .. off[v+1])
  *   cols  m_hat int32      ascending within each list
- *   tasks 4*tasks uint32   one record per task, sorted by (class, owner, partner), the
- *                          small class first: owner, partner, start of N+(partner) in
- *                          cols, |N+(partner)|
+ *   tasks 4*tasks uint32   one record per task: owner, partner, start of N+(partner) in
+ *                          cols, |N+(partner)|; the small class first, then by owner, and
+ *                          an owner's tasks in the order of their oriented edges in cols
  * Any output pointer may be NULL.
  */
 tc_status tc_graph_csr(tc_graph_t g, const int32_t** deg, const int64_t** off, const int32_t** cols,

@@ -68,7 +68,7 @@ def _load():
             L.or_count.restype = u64
             L.or_vertex_cost.argtypes = [ctypes.c_int, i32, P, P, P, P]
             L.or_vertex_cost.restype = ctypes.c_int
-            L.or_tasks.argtypes = [i32, P, P, i64, P, P, ctypes.POINTER(i64)]
+            L.or_tasks.argtypes = [i32, P, P, i64, P, P, P, ctypes.POINTER(i64)]
             L.or_tasks.restype = i64
             L.or_task_costs.argtypes = [ctypes.c_int, ctypes.c_int, i32, i64, i32, i32, i32, P, P, P,
                                         i64, P, P, P]
@@ -168,21 +168,25 @@ def vertex_cost(csr: OrientedCSR, fn: int) -> np.ndarray:
     return f[:csr.n]
 
 
-def tasks(csr: OrientedCSR, small_max: int = 1 << 40, with_split: bool = False):
-    """Owner-grouped tasks: (owner int32[T], partner int32[T]) sorted by (class, owner, partner),
-    small class first (owner list of at most small_max entries).  With with_split, also the
-    number of small tasks."""
+def tasks(csr: OrientedCSR, small_max: int = 1 << 40, with_split: bool = False, with_pos: bool = False):
+    """Owner-grouped tasks: (owner int32[T], partner int32[T]) sorted by (class, owner, position of
+    the oriented edge in csr.cols), small class first (owner list of at most small_max entries).
+    With with_split, also the number of small tasks; with with_pos, also the positions."""
     L = _load()
     cap = max(csr.m_hat, 1)
     o = np.empty(cap, np.int32)
     p = np.empty(cap, np.int32)
+    pos = np.empty(cap, np.int64)
     ns = ctypes.c_int64()
-    t = L.or_tasks(csr.n, _p(csr.off), _p(csr.cols), int(small_max), _p(o), _p(p), ctypes.byref(ns))
+    t = L.or_tasks(csr.n, _p(csr.off), _p(csr.cols), int(small_max), _p(o), _p(p), _p(pos), ctypes.byref(ns))
     if t < 0:
         raise OracleError(ERR_OOM)
+    out = [o[:t].copy(), p[:t].copy()]
     if with_split:
-        return o[:t].copy(), p[:t].copy(), int(ns.value)
-    return o[:t].copy(), p[:t].copy()
+        out.append(int(ns.value))
+    if with_pos:
+        out.append(pos[:t].copy())
+    return tuple(out)
 
 
 def task_costs(csr: OrientedCSR, owner, partner, model=MODEL_EDGE, fn=COST_DEGREE,

@@ -248,19 +248,23 @@ int or_vertex_cost(int fn, int32_t n, const int32_t* deg, const int64_t* off, co
  * the partner is the other one; the triangle count of the edge is
  * |N_owner intersect N_partner|.  Tasks whose partner list is empty are dropped
  * (they count nothing).  A task is "small" when its owner's list has at most
- * small_max entries, else "big".  Tasks are sorted by (class, owner, partner):
- * all small tasks first.  owner/partner need capacity m_hat; *n_small receives the
- * number of small tasks.  Returns the number of tasks, or -1 on OOM.
+ * small_max entries, else "big".  Tasks are sorted by (class, owner, position of
+ * the oriented edge in cols): all small tasks first.  owner/partner/pos need
+ * capacity m_hat (pos may be NULL); *n_small receives the number of small tasks.
+ * Returns the number of tasks, or -1 on OOM or more than 2^32 edges.
  */
 int64_t or_tasks(int32_t n, const int64_t* off, const int32_t* cols, int64_t small_max, int32_t* owner,
-                 int32_t* partner, int64_t* n_small) {
+                 int32_t* partner, int64_t* pos, int64_t* n_small) {
     int64_t mh = off[n];
+    if (mh >= ((int64_t)1 << 32)) return -1;
     uint64_t* key = (uint64_t*)malloc((size_t)(mh > 0 ? mh : 1) * sizeof(uint64_t));
-    if (!key) return -1;
+    int32_t* row = (int32_t*)malloc((size_t)(mh > 0 ? mh : 1) * sizeof(int32_t));
+    if (!key || !row) { free(key); free(row); return -1; }
     int64_t t = 0, ns = 0;
     for (int32_t v = 0; v < n; ++v) {
         int64_t dv = off[v + 1] - off[v];
         for (int64_t i = off[v]; i < off[v + 1]; ++i) {
+            row[i] = v;
             int32_t u = cols[i];
             int64_t du = off[u + 1] - off[u];
             int32_t o = dv >= du ? v : u;
@@ -268,15 +272,19 @@ int64_t or_tasks(int32_t n, const int64_t* off, const int32_t* cols, int64_t sma
             if (off[p + 1] - off[p] == 0) continue;
             uint64_t big = (off[o + 1] - off[o]) > small_max ? 1u : 0u;
             if (!big) ++ns;
-            key[t++] = (big << 63) | ((uint64_t)(uint32_t)o << 31) | (uint32_t)p;
+            key[t++] = (big << 63) | ((uint64_t)(uint32_t)o << 32) | (uint64_t)i;
         }
     }
     qsort(key, (size_t)t, sizeof(uint64_t), cmp_u64);
-    for (int64_t i = 0; i < t; ++i) {
-        owner[i] = (int32_t)((key[i] >> 31) & 0xFFFFFFFFu);
-        partner[i] = (int32_t)(key[i] & 0x7FFFFFFFu);
+    for (int64_t k = 0; k < t; ++k) {
+        int64_t i = (int64_t)(key[k] & 0xFFFFFFFFu);
+        int32_t o = (int32_t)((key[k] >> 32) & 0x7FFFFFFFu);
+        owner[k] = o;
+        partner[k] = row[i] == o ? cols[i] : row[i];
+        if (pos) pos[k] = i;
     }
     free(key);
+    free(row);
     *n_small = ns;
     return t;
 }

@@ -72,7 +72,7 @@ static void free_graph(tc_graph* g) {
     };
     put(g->deg, (size_t)(g->n > 0 ? g->n : 1) * 4);
     put(g->off, ((size_t)g->n + 1) * 8);
-    put(g->cols, (size_t)(g->m_hat > 0 ? g->m_hat : 1) * 4);
+    put(g->cols, ((size_t)(g->m_hat > 0 ? g->m_hat : 1) + 4) * 4);
     put(g->trec, (size_t)(g->tasks > 0 ? g->tasks : 1) * sizeof(TaskRec));
     put(g->own_first, (size_t)g->own_first_cap * 4);
     put(g->work.prefix, (size_t)(g->tasks + 1) * 8);

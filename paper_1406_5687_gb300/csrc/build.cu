@@ -201,11 +201,13 @@ __global__ void k_max_deg(const int32_t* __restrict__ deg, const int32_t* __rest
 }
 
 // --------------------------------------------------------------------------- tasks
-// Task key: (class << 2b) | (owner << b) | partner, class 1 when the owner's list has more
-// than small_max entries, so that the sort puts every small task first.
+// Task key: partner in the low 32 bits, then owner (b bits), class (1 when the owner's list
+// has more than small_max entries) and a drop bit (partner list empty).  The stable sort on
+// the drop/class/owner bits alone keeps each owner's tasks in the order of their oriented
+// edges in the N+ lists, puts every small task first and every dropped edge last.
 __global__ void k_task_keys(const uint64_t* __restrict__ okeys, const int32_t* __restrict__ cols, int64_t mh, int b,
-                            const int32_t* __restrict__ dhat, int small_max, uint64_t sent,
-                            uint64_t* __restrict__ tkeys, BuildCounters* cnt) {
+                            const int32_t* __restrict__ dhat, int small_max, uint64_t* __restrict__ tkeys,
+                            BuildCounters* cnt) {
     const int lane = threadIdx.x & 31;
     unsigned long long sv = 0, su = 0, ss = 0, nt = 0, nsm = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mh; i += (int64_t)gridDim.x * blockDim.x) {
@@ -216,16 +218,15 @@ __global__ void k_task_keys(const uint64_t* __restrict__ okeys, const int32_t* _
         int32_t dp = dv >= du ? du : dv;
         sv += (unsigned long long)dv;
         su += (unsigned long long)du;
+        const int32_t dop = dv >= du ? dv : du;
+        const uint64_t big = dop > small_max ? 1ull : 0ull;
+        const uint64_t drop = dp > 0 ? 0ull : 1ull;
         if (dp > 0) {
-            const int32_t dop = dv >= du ? dv : du;
-            const uint64_t big = dop > small_max ? 1ull : 0ull;
             ss += (unsigned long long)dp;
             nt += 1;
             nsm += 1ull - big;
-            tkeys[i] = (big << (2 * b)) | ((uint64_t)o << b) | p;
-        } else {
-            tkeys[i] = sent;
         }
+        tkeys[i] = (drop << (33 + b)) | (big << (32 + b)) | ((uint64_t)o << 32) | p;
     }
     sv = warp_sum(sv);
     su = warp_sum(su);
@@ -260,7 +261,7 @@ __global__ void k_task_records(const uint64_t* __restrict__ tkeys, int64_t T, in
     const uint64_t mask = (1ull << b) - 1;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
         uint64_t k = tkeys[t];
-        uint32_t o = (uint32_t)((k >> b) & mask), p = (uint32_t)(k & mask);
+        uint32_t o = (uint32_t)((k >> 32) & mask), p = (uint32_t)(k & 0xFFFFFFFFu);
         int64_t s = off[p], e = off[p + 1];
         TaskRec r;
         r.owner = o;
@@ -285,9 +286,19 @@ static unsigned grid_stride_blocks(int64_t n) {
     return (unsigned)(want < cap ? want : cap);
 }
 
+// Synchronise and return the handle's device error word (set by a bounded wait that gave up).
+static tc_status check_device_error(tc_graph* g, cudaStream_t s) {
+    DevStatus h;
+    TC_CUDA_TRY(cudaMemcpyAsync(&h, g->status, sizeof(h), cudaMemcpyDeviceToHost, s));
+    TC_CUDA_TRY(cudaStreamSynchronize(s));
+    return h.code != 0 ? (tc_status)h.code : TC_OK;
+}
+
 tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t m, int32_t n, cudaStream_t s) {
     Allocator* al = &g->al;
+    const long long spin = g->opt.retry_limit > 0 ? g->opt.retry_limit : (1ll << 20);
     const int b = bits_for(n);
+    if (b > 30) return TC_ERR_UNSUPPORTED;  // task keys hold 32 + b + 2 bits
     const int nbits = 2 * b;
     const uint64_t sent = (nbits >= 64) ? ~0ull : ((1ull << nbits) - 1);
     g->n = n;
@@ -313,7 +324,8 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     TC_CUDA_TRY(cudaGetLastError());
     // a2
     uint64_t* sorted = nullptr;
-    TC_TRY(radix_sort_u64(ka.ptr, kb.ptr, m, nbits, al, s, &sorted));
+    TC_TRY(radix_sort_u64(ka.ptr, kb.ptr, m, 0, nbits, al, s, &sorted, g->status, spin));
+    TC_TRY(check_device_error(g, s));
     uint64_t* other = sorted == ka.ptr ? kb.ptr : ka.ptr;
     uint64_t mh64 = 0;
     TC_TRY(compact(UniquePred{sorted, sent}, KeyVal{sorted}, m, other, al, s, &mh64));
@@ -351,7 +363,8 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     }
     TC_CUDA_TRY(cudaGetLastError());
     uint64_t* osorted = nullptr;
-    TC_TRY(radix_sort_u64(spare, ukeys, mh, nbits, al, s, &osorted));
+    TC_TRY(radix_sort_u64(spare, ukeys, mh, 0, nbits, al, s, &osorted, g->status, spin));
+    TC_TRY(check_device_error(g, s));
     uint64_t* free_buf = osorted == spare ? ukeys : spare;
     // a5
     if (mh > 0) {
@@ -361,7 +374,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     DevBuf<int64_t> off;
     DevBuf<int32_t> cols;
     TC_TRY(off.alloc(al, (size_t)n + 1, s));
-    TC_TRY(cols.alloc(al, mh > 0 ? mh : 1, s));
+    TC_TRY(cols.alloc(al, (size_t)(mh > 0 ? mh : 1) + 4, s));  // +4: 16-byte vector reads may run past the end
     {
         // offsets = exclusive scan of dhat (values < 2^63, so the uint64 scan is the int64 array)
         DevBuf<uint64_t> scr;
@@ -379,16 +392,15 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     TC_CUDA_TRY(cudaGetLastError());
 
     // tasks
-    // task keys carry one more bit (the class); their sentinel is all ones over 2b + 1 bits
-    const uint64_t tsent = (1ull << (nbits + 1)) - 1;
     if (mh > 0) {
         k_task_keys<<<grid_stride_blocks(mh), kThreads, 0, s>>>(osorted, cols.ptr, mh, b, dhat.ptr,
-                                                                g->opt.small_max, tsent, free_buf, cnt.ptr);
+                                                                g->opt.small_max, free_buf, cnt.ptr);
         note_launch();
     }
     TC_CUDA_TRY(cudaGetLastError());
     uint64_t* tsorted = nullptr;
-    TC_TRY(radix_sort_u64(free_buf, osorted, mh, nbits + 1, al, s, &tsorted));
+    TC_TRY(radix_sort_u64(free_buf, osorted, mh, 32, b + 2, al, s, &tsorted, g->status, spin));
+    TC_TRY(check_device_error(g, s));
     TC_CUDA_TRY(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(hc), cudaMemcpyDeviceToHost, s));
     TC_CUDA_TRY(cudaStreamSynchronize(s));
     const int64_t T = (int64_t)hc.tasks;
@@ -427,7 +439,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     g->cols = cols.detach();
     g->trec = rec.detach();
     g->bytes = (int64_t)align_up((size_t)(n > 0 ? n : 1) * 4, 256) + (int64_t)align_up(((size_t)n + 1) * 8, 256) +
-               (int64_t)align_up((size_t)(mh > 0 ? mh : 1) * 4, 256) +
+               (int64_t)align_up(((size_t)(mh > 0 ? mh : 1) + 4) * 4, 256) +
                (int64_t)align_up((size_t)(T > 0 ? T : 1) * sizeof(TaskRec), 256) +
                (int64_t)align_up((size_t)g->own_first_cap * 4, 256);
     TC_CUDA_TRY(cudaStreamSynchronize(s));

@@ -140,19 +140,56 @@ __device__ __forceinline__ HashView make_view(uint32_t* tbl, uint32_t cap) {
     return hv;
 }
 
+// Linear probing that starts at an even slot: the table is read as buckets of two slots,
+// so one 8-byte shared load covers the first two probes of a lookup.
+__device__ __forceinline__ uint32_t hash_start(const HashView& hv, uint32_t x) {
+    return ((x * kHashMul) >> (hv.shift + 1)) << 1;
+}
+
 __device__ __forceinline__ void hash_insert(const HashView& hv, uint32_t x) {
-    uint32_t h = (x * kHashMul) >> hv.shift;
+    uint32_t h = hash_start(hv, x);
     while (atomicCAS(&hv.tbl[h], kEmpty, x) != kEmpty) h = (h + 1) & hv.cmask;
 }
 
-__device__ __forceinline__ bool hash_probe(const HashView& hv, uint32_t w) {
-    uint32_t h = (w * kHashMul) >> hv.shift;
+// Continue a lookup of w from slot h (the first bucket was full of other keys).
+__device__ __noinline__ bool hash_probe_rest(const HashView& hv, uint32_t w, uint32_t h) {
     for (;;) {
         const uint32_t s = hv.tbl[h];
         if (s == w) return true;
         if (s == kEmpty) return false;
         h = (h + 1) & hv.cmask;
     }
+}
+
+__device__ __forceinline__ bool hash_probe(const HashView& hv, uint32_t w) {
+    const uint32_t h = hash_start(hv, w);
+    const uint2 b = *reinterpret_cast<const uint2*>(hv.tbl + h);
+    if (b.x == w || b.y == w) return true;
+    if (b.x == kEmpty || b.y == kEmpty) return false;
+    return hash_probe_rest(hv, w, (h + 2) & hv.cmask);
+}
+
+// First-bucket lookups of N entries issued together.  Returns the hits; entries whose
+// bucket held two other keys are flagged in `more` (bit k) for hash_probe_rest.
+template <int N>
+__device__ __forceinline__ uint32_t probe_batch(const HashView& hv, const uint32_t (&w)[N], const bool (&valid)[N],
+                                                uint32_t& more) {
+    uint32_t h[N];
+    uint2 b[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) h[k] = hash_start(hv, w[k]);
+#pragma unroll
+    for (int k = 0; k < N; ++k) b[k] = *reinterpret_cast<const uint2*>(hv.tbl + h[k]);
+    uint32_t hits = 0;
+    more = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const bool hit = b[k].x == w[k] || b[k].y == w[k];
+        const bool end = b[k].x == kEmpty || b[k].y == kEmpty;
+        hits += (valid[k] && hit) ? 1u : 0u;
+        more |= (valid[k] && !hit && !end) ? (1u << k) : 0u;
+    }
+    return hits;
 }
 
 // Bit position of the set bit of m that has exactly k set bits below it (0 <= k < popc(m)):
@@ -188,37 +225,65 @@ __device__ __forceinline__ HashView region_view(uint32_t* tbl, uint32_t reg) {
 // One warp counts a batch of nb <= 32 tasks (lane i holds task i's record and, in
 // `reg`, the table region of that task's owner) against the staged owner lists.
 template <bool EXTRA>
-__device__ void warp_batch(const CountArgs& a, const TaskRec& r, int nb, uint32_t* __restrict__ tbl, uint32_t reg,
-                           int lane, unsigned long long& acc) {
+__device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskRec& r, int nb, uint32_t* __restrict__ tbl,
+                                                 uint32_t reg, int lane, uint32_t& cnt) {
     const uint32_t len = lane < nb ? r.plen : 0u;
-    // partner lists of 32 or more entries: the whole warp streams one list at a time
-    unsigned longm = __ballot_sync(kFull, len >= 32u);
-    while (longm) {
-        const int j = __ffs(longm) - 1;
-        longm &= longm - 1;
-        const uint32_t s = __shfl_sync(kFull, r.pstart, j);
-        const uint32_t L = __shfl_sync(kFull, len, j);
-        const HashView hv = region_view(tbl, __shfl_sync(kFull, reg, j));
-        uint32_t pj = 0, oj = 0;
-        if (EXTRA) {
-            pj = __shfl_sync(kFull, r.partner, j);
-            oj = __shfl_sync(kFull, r.owner, j);
-        }
-        const int32_t* __restrict__ lst = a.cols + s;
-        for (uint32_t base = 0; base < L; base += 32u * kUnroll) {
-            uint32_t wv[kUnroll];
-            bool ok[kUnroll];
+    // Partner lists of 32 or more entries are cut into chunks of 128 entries aligned to 16
+    // bytes; the warp takes four chunks per step (possibly of different lists), each lane
+    // loading one int4 of each.  A chunk is warp-uniform, so its list is found with one
+    // ballot over the lanes' chunk prefix.
+    {
+        const bool lng = len >= 32u;
+        const uint32_t s0 = r.pstart & ~3u;                               // 16-byte aligned start
+        const uint32_t nch = lng ? (((r.pstart & 3u) + len + 127u) >> 7) : 0u;  // chunks of this list
+        const uint32_t cincl = warp_inclusive_scan(nch, lane);
+        const uint32_t cexcl = cincl - nch;
+        const uint32_t ctot = __shfl_sync(kFull, cincl, 31);
+        for (uint32_t c0 = 0; c0 < ctot; c0 += 4) {
+            int4 v[4];
+            uint32_t lo[4], hi[4], e0[4], rg[4];
+            uint32_t ow[4], pa[4];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const uint32_t i = base + 32u * u + lane;
-                ok[u] = i < L;
-                wv[u] = ok[u] ? (uint32_t)__ldg(lst + i) : 0u;
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t c = c0 + u;
+                const unsigned who = __ballot_sync(kFull, nch != 0u && cexcl <= c);
+                const int j = 31 - __clz(who);  // list holding chunk c (any lane when c >= ctot)
+                const uint32_t it = c - __shfl_sync(kFull, cexcl, j);
+                lo[u] = __shfl_sync(kFull, r.pstart, j);
+                hi[u] = lo[u] + __shfl_sync(kFull, len, j);
+                rg[u] = __shfl_sync(kFull, reg, j);
+                if (EXTRA) {
+                    ow[u] = __shfl_sync(kFull, r.owner, j);
+                    pa[u] = __shfl_sync(kFull, r.partner, j);
+                }
+                e0[u] = __shfl_sync(kFull, s0, j) + it * 128u + 4u * (uint32_t)lane;
+                if (c < ctot && e0[u] < hi[u]) v[u] = __ldg(reinterpret_cast<const int4*>(a.cols + e0[u]));
+                else v[u] = make_int4(-1, -1, -1, -1);
             }
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const bool hit = ok[u] && hash_probe(hv, wv[u]);
-                acc += hit ? 1ull : 0ull;
-                if (EXTRA && hit) on_hit<EXTRA>(a, oj, pj, wv[u]);
+            for (int u = 0; u < 4; ++u) {
+                if (c0 + u >= ctot) break;
+                const HashView hv = region_view(tbl, rg[u]);
+                const uint32_t xs[4] = {(uint32_t)v[u].x, (uint32_t)v[u].y, (uint32_t)v[u].z, (uint32_t)v[u].w};
+                bool ok[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) ok[k] = e0[u] + (uint32_t)k - lo[u] < hi[u] - lo[u];
+                if (!EXTRA) {
+                    uint32_t more;
+                    cnt += probe_batch<4>(hv, xs, ok, more);
+                    while (more) {
+                        const int k = __ffs(more) - 1;
+                        more &= more - 1;
+                        cnt += hash_probe_rest(hv, xs[k], (hash_start(hv, xs[k]) + 2) & hv.cmask) ? 1u : 0u;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const bool hit = ok[k] && hash_probe(hv, xs[k]);
+                        cnt += hit ? 1u : 0u;
+                        if (hit) on_hit<EXTRA>(a, ow[u], pa[u], xs[k]);
+                    }
+                }
             }
         }
     }
@@ -264,17 +329,48 @@ __device__ void warp_batch(const CountArgs& a, const TaskRec& r, int nb, uint32_
             qj[u] = q;
             before += __popc(starts);
         }
+        if (!EXTRA) {
+            // entries of different tasks may sit in different owner regions: look up each
+            // entry's first bucket, then finish the rare unresolved ones
+            uint32_t h[kUnroll];
+            uint2 b[kUnroll];
+            const uint32_t* base_p[kUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const bool hit = ok[u] && hash_probe(region_view(tbl, rg[u]), wv[u]);
-            acc += hit ? 1ull : 0ull;
-            if (EXTRA) {
+            for (int u = 0; u < kUnroll; ++u) {
+                const HashView hv = region_view(tbl, rg[u]);
+                base_p[u] = hv.tbl;
+                h[u] = hash_start(hv, wv[u]);
+                b[u] = *reinterpret_cast<const uint2*>(hv.tbl + h[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const bool hit = b[u].x == wv[u] || b[u].y == wv[u];
+                const bool end = b[u].x == kEmpty || b[u].y == kEmpty;
+                cnt += (ok[u] && hit) ? 1u : 0u;
+                if (ok[u] && !hit && !end) {
+                    const HashView hv = region_view(tbl, rg[u]);
+                    cnt += hash_probe_rest(hv, wv[u], (h[u] + 2) & hv.cmask) ? 1u : 0u;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const bool hit = ok[u] && hash_probe(region_view(tbl, rg[u]), wv[u]);
+                cnt += hit ? 1u : 0u;
                 const uint32_t pj = __shfl_sync(kFull, g_partner, qj[u]);
                 const uint32_t oj = __shfl_sync(kFull, g_owner, qj[u]);
                 if (hit) on_hit<EXTRA>(a, oj, pj, wv[u]);
             }
         }
     }
+}
+
+template <bool EXTRA>
+__device__ void warp_batch(const CountArgs& a, const TaskRec& r, int nb, uint32_t* __restrict__ tbl, uint32_t reg,
+                           int lane, unsigned long long& acc) {
+    uint32_t cnt = 0;  // this lane's hits in the batch (fits 32 bits: at most 32 lists of < 2^17 entries)
+    warp_batch_count<EXTRA>(a, r, nb, tbl, reg, lane, cnt);
+    acc += cnt;
 }
 
 // Eq. 2: take the next chunk of the class's remaining cost (one thread; bounded retries).

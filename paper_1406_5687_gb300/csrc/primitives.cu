@@ -73,70 +73,98 @@ __global__ void k_scan_single_block(uint64_t* v, int64_t n) {
 }
 
 // --------------------------------------------------------------------------- radix sort
+//
+// LSD radix sort with 8-bit digits and one kernel per digit (the "onesweep" arrangement of
+// Adinets and Merrill, 2022).  One upfront pass counts every digit of every key.  Each
+// digit pass then takes tiles of 4096 keys in the order blocks start (an atomic tile
+// counter), ranks the tile's keys stably in shared memory, publishes the tile's digit
+// counts and obtains the count of each digit in all earlier tiles by a decoupled
+// look-back over their published words (flag in the top two bits: aggregate of the tile
+// alone, or inclusive prefix), then writes every digit run of the tile contiguously.
+// A tile waits only on tiles taken earlier, whose blocks are already running; every wait
+// is bounded and sets the error word when it gives up.
 
-constexpr int kRsBlock = 512;
-constexpr int kRsWarps = kRsBlock / 32;
-constexpr int kRsItems = 16;
-constexpr int kRsTile = kRsBlock * kRsItems;  // 8192 keys
-constexpr int kRsRadix = 256;
+constexpr int kOsBlock = 256;
+constexpr int kOsWarps = kOsBlock / 32;
+constexpr int kOsItems = 16;
+constexpr int kOsTile = kOsBlock * kOsItems;  // 4096 keys
+constexpr int kRadix = 256;
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPrefix = 2ull << 62;
+constexpr unsigned long long kCountMask = (1ull << 62) - 1;
 
-struct IdentityU32 {
-    const uint32_t* v;
-    __device__ uint64_t operator()(int64_t i) const { return v[i]; }
-};
-
-__global__ void __launch_bounds__(kRsBlock) k_rs_hist(const uint64_t* __restrict__ in, int64_t n, int shift,
-                                                      int64_t ntiles, uint32_t* __restrict__ counts) {
-    __shared__ uint32_t h[kRsWarps][kRsRadix];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kRsWarps * kRsRadix; i += kRsBlock) (&h[0][0])[i] = 0;
+// Counts of every digit of every pass (npass * 256, uint64).  Each warp counts into its
+// own shared-memory copy, so atomics only collide between lanes of one warp.
+__global__ void __launch_bounds__(kOsBlock) k_os_hist(const uint64_t* __restrict__ keys, int64_t n, int lo_bit,
+                                                      int npass, unsigned long long* __restrict__ ghist) {
+    extern __shared__ unsigned hs[];  // kOsWarps * npass * 256
+    const int warp = threadIdx.x >> 5;
+    const int per_warp = npass * kRadix;
+    for (int i = threadIdx.x; i < kOsWarps * per_warp; i += kOsBlock) hs[i] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kRsTile;
-#pragma unroll 4
-    for (int j = 0; j < kRsItems; ++j) {
-        int64_t i = base + (int64_t)j * kRsBlock + threadIdx.x;
-        unsigned d = i < n ? (unsigned)((in[i] >> shift) & 0xFF) : 256u;
-        unsigned peers = __match_any_sync(kFull, d);
-        if (d < 256u && lane == __ffs(peers) - 1) h[warp][d] += __popc(peers);
+    unsigned* h = hs + warp * per_warp;
+    for (int64_t i = (int64_t)blockIdx.x * kOsBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kOsBlock) {
+        const uint64_t k = keys[i] >> lo_bit;
+        for (int p = 0; p < npass; ++p) atomicAdd(&h[p * kRadix + (unsigned)((k >> (8 * p)) & 0xFF)], 1u);
     }
     __syncthreads();
-    if (threadIdx.x < kRsRadix) {
-        uint32_t s = 0;
-#pragma unroll
-        for (int w = 0; w < kRsWarps; ++w) s += h[w][threadIdx.x];
-        counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = s;
+    for (int i = threadIdx.x; i < per_warp; i += kOsBlock) {
+        unsigned t = 0;
+        for (int w = 0; w < kOsWarps; ++w) t += hs[w * per_warp + i];
+        if (t) atomicAdd(&ghist[i], (unsigned long long)t);
     }
 }
 
-constexpr size_t kRsScatterSmem = (size_t)kRsTile * 8 + (size_t)kRsWarps * kRsRadix * 4 + 264 * 4 + kRsRadix * 8;
-
-__global__ void __launch_bounds__(kRsBlock) k_rs_scatter(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
-                                                         int64_t n, int shift, int64_t ntiles,
-                                                         const uint64_t* __restrict__ offs) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t* skeys = (uint64_t*)smem_raw;                    // kRsTile
-    uint32_t* wcnt = (uint32_t*)(skeys + kRsTile);            // kRsWarps * 256
-    uint32_t* dstart = wcnt + kRsWarps * kRsRadix;            // 256 (+ 8 for the warp totals)
-    uint64_t* goff = (uint64_t*)(dstart + 264);               // 256
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t tbase = (int64_t)blockIdx.x * kRsTile;
-    for (int i = threadIdx.x; i < kRsWarps * kRsRadix; i += kRsBlock) wcnt[i] = 0;
-    if (threadIdx.x < kRsRadix) goff[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+// Exclusive scan of each pass's 256 digit counts, in place (one block per pass).
+__global__ void k_os_bases(unsigned long long* ghist) {
+    __shared__ unsigned long long v[kRadix];
+    unsigned long long* g = ghist + (int64_t)blockIdx.x * kRadix;
+    const int d = threadIdx.x;
+    const unsigned long long own = g[d];
+    v[d] = own;
     __syncthreads();
+    for (int o = 1; o < kRadix; o <<= 1) {
+        const unsigned long long t = d >= o ? v[d - o] : 0ull;
+        __syncthreads();
+        v[d] += t;
+        __syncthreads();
+    }
+    g[d] = v[d] - own;
+}
 
-    // warp-striped load: lane l holds the warp's keys j*32 + l, j = 0..15 (memory order j-major)
-    const int64_t wbase = tbase + (int64_t)warp * 32 * kRsItems;
-    uint64_t key[kRsItems];
-    uint32_t rank[kRsItems];
-    uint32_t* mycnt = wcnt + warp * kRsRadix;
+constexpr size_t kOsSmem = (size_t)kOsTile * 8 + (size_t)kOsWarps * kRadix * 4 + 264 * 4 + kRadix * 8;
+
+__global__ void __launch_bounds__(kOsBlock, 4) k_os_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                      int64_t n, int shift, const unsigned long long* __restrict__ base,
+                                                      unsigned long long* status, unsigned* tile_counter,
+                                                      DevStatus* err, long long spin_limit) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t* skeys = (uint64_t*)smem_raw;                           // kOsTile
+    uint32_t* wcnt = (uint32_t*)(skeys + kOsTile);                   // kOsWarps * 256
+    uint32_t* dstart = wcnt + kOsWarps * kRadix;                     // 256 + 8 warp totals
+    unsigned long long* goff = (unsigned long long*)(dstart + 264);  // 256
+    __shared__ unsigned s_tile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+    for (int i = threadIdx.x; i < kOsWarps * kRadix; i += kOsBlock) wcnt[i] = 0;
+    __syncthreads();
+    const long long tile = (long long)s_tile;
+    const int64_t tbase = tile * kOsTile;
+
+    // warp-striped load: lane l holds the warp's keys j*32 + l (memory order j-major), ranked
+    // within the warp by digit
+    const int64_t wbase = tbase + (int64_t)warp * 32 * kOsItems;
+    uint64_t key[kOsItems];
+    uint32_t rank[kOsItems];
+    uint32_t* mycnt = wcnt + warp * kRadix;
 #pragma unroll
-    for (int j = 0; j < kRsItems; ++j) {
-        int64_t i = wbase + j * 32 + lane;
-        bool valid = i < n;
+    for (int j = 0; j < kOsItems; ++j) {
+        const int64_t i = wbase + j * 32 + lane;
+        const bool valid = i < n;
         key[j] = valid ? in[i] : 0;
-        unsigned d = valid ? (unsigned)((key[j] >> shift) & 0xFF) : 256u;
-        unsigned peers = __match_any_sync(kFull, d);
-        int leader = __ffs(peers) - 1;
+        const unsigned d = valid ? (unsigned)((key[j] >> shift) & 0xFF) : 256u;
+        const unsigned peers = __match_any_sync(kFull, d);
+        const int leader = __ffs(peers) - 1;
         uint32_t b = 0;
         if (lane == leader && d < 256u) {
             b = mycnt[d];
@@ -146,71 +174,106 @@ __global__ void __launch_bounds__(kRsBlock) k_rs_scatter(const uint64_t* __restr
         rank[j] = b + __popc(peers & lanemask_lt());
     }
     __syncthreads();
-    // per digit: exclusive scan over warps, then over digits
-    if (threadIdx.x < kRsRadix) {
+    if (threadIdx.x < kRadix) {
         const int d = threadIdx.x;
+        // per digit: exclusive scan over the warps; `run` ends as the tile's count of d
         uint32_t run = 0;
 #pragma unroll
-        for (int w = 0; w < kRsWarps; ++w) {
-            uint32_t t = wcnt[w * kRsRadix + d];
-            wcnt[w * kRsRadix + d] = run;
+        for (int w = 0; w < kOsWarps; ++w) {
+            const uint32_t t = wcnt[w * kRadix + d];
+            wcnt[w * kRadix + d] = run;
             run += t;
         }
-        uint32_t incl = warp_inclusive_scan(run, lane);
-        if (lane == 31) dstart[256 + warp] = incl;  // warp totals (8 warps cover 256 digits)
+        // publish the tile's count and look back for the counts of all earlier tiles
+        unsigned long long* st = status + tile * kRadix;
+        unsigned long long excl = 0;
+        if (tile == 0) {
+            *(volatile unsigned long long*)&st[d] = kFlagPrefix | run;
+        } else {
+            *(volatile unsigned long long*)&st[d] = kFlagAgg | run;
+            long long j = tile - 1;
+            long long spins = 0;
+            for (;;) {
+                const unsigned long long v = *(volatile unsigned long long*)&status[j * kRadix + d];
+                const unsigned long long f = v & ~kCountMask;
+                if (f == 0) {
+                    if (++spins > spin_limit) {
+                        set_error(err, TC_ERR_TIMEOUT, tile);
+                        break;
+                    }
+                    continue;
+                }
+                excl += v & kCountMask;
+                if (f == kFlagPrefix || j == 0) break;
+                --j;
+            }
+            *(volatile unsigned long long*)&st[d] = kFlagPrefix | (excl + run);
+        }
+        goff[d] = base[d] + excl;
+        // tile-local start of each digit: scan over the digits
+        const uint32_t incl = warp_inclusive_scan(run, lane);
+        if (lane == 31) dstart[256 + warp] = incl;
         dstart[d] = incl - run;
     }
     __syncthreads();
-    if (threadIdx.x < kRsRadix) {
+    if (threadIdx.x < kRadix) {
         uint32_t add = 0;
         for (int w = 0; w < warp; ++w) add += dstart[256 + w];
         dstart[threadIdx.x] += add;
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kRsItems; ++j) {
-        int64_t i = wbase + j * 32 + lane;
+    for (int j = 0; j < kOsItems; ++j) {
+        const int64_t i = wbase + j * 32 + lane;
         if (i < n) {
-            unsigned d = (unsigned)((key[j] >> shift) & 0xFF);
+            const unsigned d = (unsigned)((key[j] >> shift) & 0xFF);
             skeys[dstart[d] + mycnt[d] + rank[j]] = key[j];
         }
     }
     __syncthreads();
-    const int64_t valid = n - tbase < kRsTile ? n - tbase : kRsTile;
-    for (int i = threadIdx.x; i < valid; i += kRsBlock) {
-        uint64_t k = skeys[i];
-        unsigned d = (unsigned)((k >> shift) & 0xFF);
+    const int64_t valid = n - tbase < kOsTile ? n - tbase : kOsTile;
+    for (int i = threadIdx.x; i < valid; i += kOsBlock) {
+        const uint64_t k = skeys[i];
+        const unsigned d = (unsigned)((k >> shift) & 0xFF);
         out[goff[d] + (uint64_t)(i - (int)dstart[d])] = k;
     }
 }
 
 int64_t radix_sort_scratch_bytes(int64_t n) {
-    int64_t ntiles = ceil_div(n > 0 ? n : 1, kRsTile);
-    int64_t cnt = ntiles * kRsRadix;
-    return (int64_t)align_up(cnt * 4, 256) + (int64_t)align_up((cnt + 1) * 8, 256) +
-           (int64_t)align_up(scan_scratch_words(cnt) * 8, 256);
+    const int64_t ntiles = ceil_div(n > 0 ? n : 1, kOsTile);
+    return (int64_t)align_up((size_t)ntiles * kRadix * 8, 256) + 4096 + 256;
 }
 
-tc_status radix_sort_u64(uint64_t* keys, uint64_t* tmp, int64_t n, int nbits, Allocator* al, cudaStream_t s,
-                         uint64_t** result) {
+tc_status radix_sort_u64(uint64_t* keys, uint64_t* tmp, int64_t n, int lo_bit, int nbits, Allocator* al,
+                         cudaStream_t s, uint64_t** result, DevStatus* err, long long spin_limit) {
     *result = keys;
     if (n <= 1 || nbits <= 0) return TC_OK;
-    TC_CUDA_TRY(cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kRsScatterSmem));
-    const int64_t ntiles = ceil_div(n, kRsTile);
-    const int64_t cnt = ntiles * kRsRadix;
-    DevBuf<uint32_t> counts;
-    DevBuf<uint64_t> offs, scr;
-    TC_TRY(counts.alloc(al, cnt, s));
-    TC_TRY(offs.alloc(al, cnt + 1, s));
-    TC_TRY(scr.alloc(al, scan_scratch_words(cnt), s));
+    if (lo_bit < 0 || lo_bit + nbits > 64) return TC_ERR_INVALID_ARG;
+    const int npass = (nbits + 7) / 8;
+    const int64_t ntiles = ceil_div(n, kOsTile);
+    if (ntiles > 0xFFFFFFFFll) return TC_ERR_UNSUPPORTED;
+    TC_CUDA_TRY(cudaFuncSetAttribute(k_os_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOsSmem));
+    DevBuf<unsigned long long> ghist, status;
+    DevBuf<unsigned> counters;
+    TC_TRY(ghist.alloc(al, (size_t)npass * kRadix, s));
+    TC_TRY(status.alloc(al, (size_t)ntiles * kRadix, s));
+    TC_TRY(counters.alloc(al, (size_t)npass, s));
+    TC_CUDA_TRY(cudaMemsetAsync(ghist.ptr, 0, sizeof(unsigned long long) * npass * kRadix, s));
+    TC_CUDA_TRY(cudaMemsetAsync(counters.ptr, 0, sizeof(unsigned) * npass, s));
+    const int64_t hblocks = ntiles < (int64_t)num_sms() * 8 ? ntiles : (int64_t)num_sms() * 8;
+    const size_t hsmem = (size_t)kOsWarps * npass * kRadix * sizeof(unsigned);
+    TC_CUDA_TRY(cudaFuncSetAttribute(k_os_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
+    k_os_hist<<<(unsigned)hblocks, kOsBlock, hsmem, s>>>(keys, n, lo_bit, npass, ghist.ptr);
+    note_launch();
+    k_os_bases<<<npass, kRadix, 0, s>>>(ghist.ptr);
+    note_launch();
+    TC_CUDA_TRY(cudaGetLastError());
     uint64_t* a = keys;
     uint64_t* b = tmp;
-    for (int shift = 0; shift < nbits; shift += 8) {
-        k_rs_hist<<<(unsigned)ntiles, kRsBlock, 0, s>>>(a, n, shift, ntiles, counts.ptr);
-        note_launch();
-        TC_CUDA_TRY(scan_exclusive(IdentityU32{counts.ptr}, cnt, offs.ptr, scr.ptr, s));
-        k_rs_scatter<<<(unsigned)ntiles, kRsBlock, kRsScatterSmem, s>>>(a, b, n, shift, ntiles, offs.ptr);
+    for (int p = 0; p < npass; ++p) {
+        TC_CUDA_TRY(cudaMemsetAsync(status.ptr, 0, sizeof(unsigned long long) * ntiles * kRadix, s));
+        k_os_pass<<<(unsigned)ntiles, kOsBlock, kOsSmem, s>>>(a, b, n, lo_bit + 8 * p, ghist.ptr + (int64_t)p * kRadix,
+                                                               status.ptr, counters.ptr + p, err, spin_limit);
         note_launch();
         TC_CUDA_TRY(cudaGetLastError());
         uint64_t* t = a;

@@ -51,9 +51,12 @@ def test_tasks_cover_each_oriented_edge_once_and_preserve_the_count():
     n, s, d, csr = _csr(4)
     Nplus, _ = _sets(csr)
     dh = np.diff(csr.off)
-    owner, partner = oracle.tasks(csr)
-    keys = owner.astype(np.int64) * n + partner
-    assert np.all(np.diff(keys) > 0)  # sorted by (owner, partner), no repeats
+    owner, partner, pos = oracle.tasks(csr, with_pos=True)
+    keys = owner.astype(np.int64) * (csr.m_hat + 1) + pos
+    assert np.all(np.diff(keys) > 0)  # sorted by (owner, position of the oriented edge), no repeats
+    rows = np.searchsorted(csr.off, pos, side="right") - 1
+    for o_, p_, i_, r_ in zip(owner.tolist(), partner.tolist(), pos.tolist(), rows.tolist()):
+        assert {o_, p_} == {r_, int(csr.cols[i_])}  # the task is the oriented edge at position i_
     seen = set()
     for o, p in zip(owner.tolist(), partner.tolist()):
         assert dh[o] >= dh[p] >= 1
@@ -174,8 +177,9 @@ def test_task_classes_split_by_owner_list_length():
         o, p, ns = oracle.tasks(csr, small_max=k, with_split=True)
         assert set(zip(o.tolist(), p.tolist())) == set(zip(o_all.tolist(), p_all.tolist()))
         assert np.all(dh[o[:ns]] <= k) and np.all(dh[o[ns:]] > k)
+        _, _, pos = oracle.tasks(csr, small_max=k, with_pos=True)
         for lo, hi in ((0, ns), (ns, len(o))):
-            key = o[lo:hi].astype(np.int64) * n + p[lo:hi]
+            key = o[lo:hi].astype(np.int64) * (csr.m_hat + 1) + pos[lo:hi]
             assert np.all(np.diff(key) > 0)
 
 
