@@ -273,6 +273,31 @@ tc_status tc_count_ex(tc_graph_t g, const tc_options* opt, tc_stream_t stream, u
  * all handles); differences around a region count the launches inside it. */
 int64_t tc_kernel_launches(void);
 
+/*
+ * Count without allocating.  The paper has no counterpart: this exists for callers that
+ * must not allocate device memory at count time -- code that owns all device memory
+ * through its own pool, runs where an allocation could block or is not permitted, or
+ * has no room left to give.  It is tc_count_async with the count's scratch (the cost
+ * prefix of at most TC_COUNT_STATIC_MAX_TASKS + 1 entries, the scan's partial sums and
+ * the two schedule records, about 4 MiB) held in one fixed device array that the library
+ * declares statically; every GPU that loads the library keeps that array until the
+ * process exits.  It never calls cudaMalloc, cudaFree or any other allocating routine.
+ *   g          a built graph (its arrays are the inputs); its options must use
+ *              TC_COST_EDGE or TC_COST_MERGE (per-vertex cost models need a per-vertex
+ *              array: TC_ERR_INVALID_ARG).
+ *   total_dev  device, one uint64; receives T when the stream reaches it (output).
+ * Errors: TC_ERR_UNSUPPORTED when the graph has more than TC_COUNT_STATIC_MAX_TASKS
+ * tasks (tc_graph_info.tasks); TC_ERR_INVALID_ARG; TC_ERR_CUDA.  Device-side errors are
+ * reported by tc_graph_check.
+ * The first call on a device looks up the array's device address on that device; make
+ * that first call before any stream capture.  Every call shares the one array and
+ * leaves its contents behind (each call rewrites what it reads), so calls whose work
+ * overlaps on the GPU -- on different streams, or on the same graph from several
+ * threads -- race and give wrong totals: serialise them.
+ */
+#define TC_COUNT_STATIC_MAX_TASKS (1ll << 19)
+tc_status tc_count_static(tc_graph_t g, tc_stream_t stream, uint64_t* total_dev);
+
 /* ------------------------------------------------------------------ batch */
 
 typedef struct tc_batch* tc_batch_t;

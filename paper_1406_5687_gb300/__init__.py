@@ -132,6 +132,12 @@ class Graph:
         _lib.check(load().tc_count_async(self._h, _stream(stream), ctypes.c_void_p(out.data_ptr())),
                    "tc_count_async")
 
+    def count_static(self, out, stream=None):
+        """Enqueue the count without allocating (scratch in the library's fixed device array);
+        `out` is a CUDA int64 tensor with at least one element."""
+        _lib.check(load().tc_count_static(self._h, _stream(stream), ctypes.c_void_p(out.data_ptr())),
+                   "tc_count_static")
+
     def check(self, stream=None):
         _lib.check(load().tc_graph_check(self._h, _stream(stream)), "tc_graph_check")
 

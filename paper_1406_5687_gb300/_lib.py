@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_VERTEX_RANGE", 3
 TC_COST_EDGE, TC_COST_MERGE, TC_COST_ONE, TC_COST_DEGREE, TC_COST_PATRIC, TC_COST_NEW = range(6)
 TC_FN_ONE, TC_FN_DEGREE, TC_FN_PATRIC, TC_FN_NEW = range(4)
 TC_INPUT_SANITIZE, TC_INPUT_STRICT = 0, 1
+TC_COUNT_STATIC_MAX_TASKS = 1 << 19  # include/tc.h
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -89,6 +90,7 @@ SIGNATURES = {
     "tc_count_ex": (ctypes.c_int, [P, ctypes.POINTER(Options), P, ctypes.POINTER(ctypes.c_uint64),
                                    ctypes.POINTER(CountTrace)]),
     "tc_kernel_launches": (ctypes.c_int64, []),
+    "tc_count_static": (ctypes.c_int, [P, P, P]),
     "tc_batch_create": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(Options), P, ctypes.POINTER(P)]),
     "tc_batch_run": (ctypes.c_int, [P, P, P]),
     "tc_batch_free": (None, [P]),

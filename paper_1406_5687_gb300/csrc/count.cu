@@ -26,6 +26,8 @@
 //
 // Reduction.  Each warp sums its hits in registers, then one uint64 atomicAdd per warp:
 // exact and independent of order.
+#include <mutex>
+
 #include "graph.cuh"
 #include "scan.cuh"
 
@@ -993,3 +995,126 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
 }
 
 }  // namespace tcg
+
+// --------------------------------------------------------------------------- count without allocation
+//
+// tc_count_static: the same count (cost prefix, Eq. 1 / Eq. 2 schedule, both count kernels)
+// with its scratch -- the cost prefix, the scan's tile sums and the two schedule records --
+// in one file-scope device array instead of memory allocated for the handle.  Host code
+// never uses the array's name as an address: the address is asked of the runtime once per
+// device (cudaGetSymbolAddress) and passed to the kernels.
+
+namespace tcg {
+
+constexpr long long kStaticMaxTasks = TC_COUNT_STATIC_MAX_TASKS;  // a 4 MiB cost prefix
+constexpr long long kStaticPrefixWords = kStaticMaxTasks + 1;
+constexpr long long kStaticScanWords = 512;  // scan_scratch_words(kStaticMaxTasks) = 257
+constexpr long long kStaticSchedWords = (2 * sizeof(Sched) + 7) / 8;
+constexpr long long kStaticWords = kStaticPrefixWords + kStaticScanWords + kStaticSchedWords;
+
+static __device__ __align__(256) unsigned long long g_static_scratch[kStaticWords];
+
+static std::mutex g_static_mu;
+static unsigned long long* g_static_ptr[64] = {nullptr};
+
+// Device address of g_static_scratch on the current device (looked up on first use).
+static tc_status static_scratch(unsigned long long** out) {
+    int dev = 0;
+    TC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return TC_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        TC_CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
+        g_static_ptr[dev] = (unsigned long long*)p;
+    }
+    *out = g_static_ptr[dev];
+    return TC_OK;
+}
+
+static tc_status count_enqueue_static(tc_graph* g, cudaStream_t s, unsigned long long* total_dev) {
+    const tc_options& opt = g->opt;
+    if (opt.cost_model != TC_COST_EDGE && opt.cost_model != TC_COST_MERGE) return TC_ERR_INVALID_ARG;
+    const long long T = g->tasks, Ts = g->tasks_small;
+    if (T > kStaticMaxTasks) return TC_ERR_UNSUPPORTED;
+    static_assert(kStaticScanWords >= 257, "scan scratch for kStaticMaxTasks tasks");
+    unsigned long long* base = nullptr;
+    TC_TRY(static_scratch(&base));
+    uint64_t* prefix = (uint64_t*)base;
+    uint64_t* scan_scr = (uint64_t*)(base + kStaticPrefixWords);
+    Sched* sched = (Sched*)(base + kStaticPrefixWords + kStaticScanWords);
+
+    const int wpb = opt.warps_per_block;
+    const int slots_s = small_table_slots(opt.small_max);
+    const size_t smem_s = (size_t)wpb * slots_s * sizeof(uint32_t);
+    const int threads_b = opt.big_warps * 32;
+    const int slots_b = 8 * opt.piece;
+    const size_t smem_b = (size_t)slots_b * sizeof(uint32_t);
+    int blocks_s = 0, blocks_b = 0;
+    TC_TRY(grid_for_kernel(k_count_small<false>, wpb * 32, smem_s, opt.blocks_per_sm, &blocks_s));
+    TC_TRY(grid_for_kernel(k_count_big<false>, threads_b, smem_b, opt.blocks_per_sm, &blocks_b));
+    const long long W_s = blocks_s, W_b = blocks_b;
+
+    TaskCost tcf{g->trec, T, g->off, nullptr, opt.cost_model, (uint32_t)opt.piece, (uint32_t)opt.small_max,
+                 (uint32_t)opt.c_task, (uint32_t)opt.c_owner};
+    TC_CUDA_TRY(scan_exclusive(tcf, T, prefix, scan_scr, s));
+    k_sched_init<<<1, 1, 0, s>>>(sched, prefix, Ts, T, W_s, W_b, opt.static_percent, opt.min_chunk);
+    note_launch();
+    TC_CUDA_TRY(cudaGetLastError());
+    TC_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(unsigned long long), s));
+
+    CountArgs a;
+    a.off = g->off;
+    a.cols = g->cols;
+    a.tasks = g->trec;
+    a.deg = g->deg;
+    a.P = prefix;
+    a.trace_sched = sched;
+    a.total = total_dev;
+    a.t_v = nullptr;
+    a.per_edge = nullptr;
+    a.trace_chunks = nullptr;
+    a.trace_cap = 0;
+    a.trace_busy = nullptr;
+    a.status = g->status;
+    a.retry_limit = opt.retry_limit > 0 ? opt.retry_limit : (1ll << 24);
+    a.own_first = g->own_first;
+    a.n_owners = g->owners_big;
+    a.t_begin = 0;
+    a.t_end = Ts;
+    a.sched = sched;
+    a.W = W_s;
+    a.cls = 0;
+    a.piece = opt.piece;
+    a.table_slots = slots_s;
+    a.warps_per_block = wpb;
+    a.busy_offset = 0;
+    if (Ts > 0) {
+        k_count_small<false><<<blocks_s, wpb * 32, smem_s, s>>>(a);
+        note_launch();
+        TC_CUDA_TRY(cudaGetLastError());
+    }
+    a.t_begin = Ts;
+    a.t_end = T;
+    a.sched = sched + 1;
+    a.W = W_b;
+    a.cls = 1;
+    a.table_slots = slots_b;
+    a.warps_per_block = opt.big_warps;
+    a.busy_offset = W_s;
+    if (T > Ts) {
+        k_count_big<false><<<blocks_b, threads_b, smem_b, s>>>(a);
+        note_launch();
+        TC_CUDA_TRY(cudaGetLastError());
+    }
+    return TC_OK;
+}
+
+}  // namespace tcg
+
+extern "C" tc_status tc_count_static(tc_graph_t g, tc_stream_t stream, uint64_t* total_dev) {
+    if (!g || !total_dev) return TC_ERR_INVALID_ARG;
+    g->last_stream = (cudaStream_t)stream;
+    return tcg::count_enqueue_static(g, (cudaStream_t)stream, (unsigned long long*)total_dev);
+}
+
