@@ -42,6 +42,7 @@ WORKLOAD_TEXT = {
 CPU_SAMPLE_PAIRS = {"cl": 32_000_000, "ba": 16_000_000, "er": 100_000, "cl_small": 8_000_000}
 # input pairs per step of the reference (oracle) arm, so that --steps K --warmup W ends in minutes
 REF_SAMPLE_PAIRS = {"cl": 4_000_000, "ba": 2_000_000, "er": 100_000, "cl_small": 2_000_000}
+REF_BATCH_GRAPHS = 8
 
 
 def parse_args():
@@ -49,10 +50,14 @@ def parse_args():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--workload", default="cl", choices=["cl", "ba", "er", "cl_small"])
+    p.add_argument("--workload", default="cl", choices=["cl", "ba", "er", "cl_small", "batch"])
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain leg")
+    p.add_argument("--batch-graphs", type=int, default=0,
+                   help="graphs of the batched workload (default: 512 as a leg of a single-graph run, "
+                        "4096 with --workload batch)")
     return p.parse_args()
 
 
@@ -200,11 +205,189 @@ def cpu_baseline(workload, pairs, threads=1):
                       f"oracle end to end (simple graph, Fig. 1 lists, Fig. 1 count), {dt:.2f} s"}
 
 
+# --------------------------------------------------------------------------- batched and plain
+
+BATCH_TEXT = ("batched: graphs of the 4096-graph workload, seed 3 (even index Erdos-Renyi, odd index "
+              "Barabasi-Albert; n log-uniform in [1e3, 2e5]; average degree uniform in [8, 128])")
+
+
+def batch_inputs(count, threads=None):
+    """The first `count` graphs of the batched workload, generated in parallel, each edge list
+    in pinned host memory: [(src, dst, n)]."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    from graphgen import workloads as W
+    specs = W.batch_specs(count)
+
+    def gen(sp):
+        s, d = sp.edges()
+        return torch.from_numpy(s).pin_memory(), torch.from_numpy(d).pin_memory(), sp.n
+
+    with ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 4) as ex:
+        return list(ex.map(gen, specs))
+
+
+def batch_leg(count, steps, warmup, tune_sample=64, oracle_sample=4):
+    """Batched counting of `count` graphs against the plain per-graph path on the same GPU.
+
+    batched: tc_batch_build + tc_batch_run per step (edge lists resident in HBM, then from
+    pinned host memory for e2e); plain: tc_build + tc_count + tc_free per graph.  Both use the
+    options the autotuner picks on the first `tune_sample` graphs."""
+    import numpy as np
+    import torch
+    import paper_1406_5687_gb300 as tc
+    t0 = time.perf_counter()
+    host = batch_inputs(count)
+    gen_s = time.perf_counter() - t0
+    dev = [(s.cuda(non_blocking=True), d.cuda(non_blocking=True), n) for s, d, n in host]
+    torch.cuda.synchronize()
+    m_in = sum(int(s.numel()) for s, _, _ in host)
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    best, rep = tc.autotune(dev[:tune_sample], reps=2, stream=stream)
+    tune_s = time.perf_counter() - t0
+    chosen = {k: getattr(best, k) for k in ("small_max", "warps_per_block", "big_warps", "piece", "static_percent")}
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    # batched, edge lists resident in HBM: build + count per step
+    def batched_step(graphs):
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record(stream)
+        b = tc.Batch.build(graphs, options=best, stream=stream)
+        e1.record(stream)
+        out = torch.empty(count, dtype=torch.int64, device="cuda")
+        b.run(out, stream)
+        e2.record(stream)
+        b.check(stream)
+        e2.synchronize()
+        info = b.info()
+        b.free()
+        return e0.elapsed_time(e2), e0.elapsed_time(e1), e1.elapsed_time(e2), out, info
+
+    for _ in range(warmup):
+        batched_step(dev)
+    l0 = tc.kernel_launches()
+    res = [batched_step(dev) for _ in range(steps)]
+    launches = (tc.kernel_launches() - l0) // steps
+    totals = res[-1][3].cpu().numpy().astype(np.uint64)
+    info = res[-1][4]
+    b_ms = statistics.mean(r[0] for r in res)
+    b_build = statistics.mean(r[1] for r in res)
+    b_count = statistics.mean(r[2] for r in res)
+
+    # count only, CSR resident: replays of the captured launch
+    b = tc.Batch.build(dev, options=best, stream=stream)
+    out = torch.empty(count, dtype=torch.int64, device="cuda")
+    for _ in range(warmup):
+        b.run(out, stream)
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    for _ in range(steps):
+        b.run(out, stream)
+    e1.record(stream)
+    b.check(stream)
+    replay_ms = e0.elapsed_time(e1) / steps
+    if not np.array_equal(out.cpu().numpy().astype(np.uint64), totals):
+        raise RuntimeError("batched totals changed between runs")
+    edges = b.graph_edges()
+    b.free()
+
+    # e2e: edge lists in pinned host memory, the k totals read back to the host
+    def batched_host():
+        t = time.perf_counter()
+        bb = tc.Batch.build(host, options=best, stream=stream)
+        got = bb.count(stream)
+        bb.free()
+        return (time.perf_counter() - t) * 1e3, got
+    batched_host()
+    e2e = [batched_host() for _ in range(steps)]
+    if not np.array_equal(e2e[-1][1], totals):
+        raise RuntimeError("batched e2e totals differ")
+    e2e_ms = statistics.mean(x[0] for x in e2e)
+
+    # plain: one graph at a time through tc_build + tc_count, same options
+    def plain_pass(graphs):
+        tot = np.zeros(count, np.uint64)
+        cnt_ms = 0.0
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for j, (s, d, n) in enumerate(graphs):
+            g = tc.Graph.build(s, d, n, best, stream=stream)
+            c0 = time.perf_counter()
+            tot[j] = g.count(stream)
+            cnt_ms += (time.perf_counter() - c0) * 1e3
+            g.free()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) * 1e3, cnt_ms, tot
+    plain_pass(dev[:min(count, 64)])
+    p_ms, p_count_ms, p_tot = plain_pass(dev)
+    p_host_ms, _, _ = plain_pass(host)
+    if not np.array_equal(p_tot, totals):
+        raise RuntimeError("plain and batched totals differ")
+
+    # the oracle on a few of the graphs, one by one
+    import oracle
+    picks = list(range(0, count, max(1, count // oracle_sample)))[:oracle_sample]
+    for j in picks:
+        s, d, n = host[j]
+        want = oracle.count_edges(n, s.numpy(), d.numpy())
+        if want != int(totals[j]):
+            raise RuntimeError(f"graph {j}: batched {int(totals[j])} != oracle {want}")
+    return {
+        "workload": BATCH_TEXT, "graphs": count, "m_input": m_in, "m_hat": int(edges.sum()),
+        "packs": info["packs"], "triangles": int(totals.sum()), "unit": "graphs/s",
+        "batched": {"graphs_per_s": count / (b_ms / 1e3), "ms": b_ms, "build_ms": b_build, "count_ms": b_count,
+                    "count_only_graphs_per_s": count / (replay_ms / 1e3), "replay_ms": replay_ms,
+                    "e2e_graphs_per_s": count / (e2e_ms / 1e3), "e2e_ms": e2e_ms, "gpu_launches_per_step": launches},
+        "plain": {"graphs_per_s": count / (p_ms / 1e3), "ms": p_ms,
+                  "count_only_graphs_per_s": count / (p_count_ms / 1e3), "count_ms": p_count_ms,
+                  "e2e_graphs_per_s": count / (p_host_ms / 1e3), "e2e_ms": p_host_ms},
+        "speedup": {"build_and_count": p_ms / b_ms, "count_only": p_count_ms / replay_ms, "e2e": p_host_ms / e2e_ms},
+        "autotune": {"sample_graphs": min(tune_sample, count), "tried": rep["tried"], "chosen": chosen,
+                     "best_ms": rep["best_ms"], "default_ms": rep["default_ms"], "seconds": tune_s},
+        "oracle_checked_graphs": picks, "generate_s": gen_s,
+        "timing": "batched: CUDA events on the launching stream; plain: host wall clock around each "
+                  "synchronous call (the plain path returns each total to the host)",
+    }
+
+
 # --------------------------------------------------------------------------- reference arm
+
+def run_reference_batch(args):
+    """The oracle, graph by graph, on the first graphs of the batched workload (a bounded
+    sample per step): graphs/s on the host."""
+    import oracle
+    from graphgen import workloads as W
+    specs = W.batch_specs(REF_BATCH_GRAPHS)
+    graphs = [(sp.n,) + sp.edges() for sp in specs]
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for n, s, d in graphs:
+            oracle.count_edges(n, s, d)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    mean = sum(times) / len(times)
+    value = len(graphs) / mean
+    line = {"impl": "reference", "metric": "batched graphs/s", "value": value, "unit": "graphs/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": BATCH_TEXT, "graphs": len(graphs)},
+            "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {len(graphs)} graphs of the batched workload per step, oracle end to "
+                                       "end, one graph after another, single thread"},
+            "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
 
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
+    if args.workload == "batch":
+        return run_reference_batch(args)
     import oracle
     from graphgen import workloads as W
     spec = W.SINGLE[args.workload]
@@ -240,12 +423,55 @@ def run_reference(args, rank, world):
 
 # --------------------------------------------------------------------------- GPU arm
 
+def run_batch_only(args, rank, world, local):
+    """--workload batch: the batched leg alone at its full size, as the JSON line's metric."""
+    import torch
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    count = args.batch_graphs or 4096
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get(
+        "CUDA_VISIBLE_DEVICES") else str(local)
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    leg = batch_leg(count, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms = leg["batched"]["ms"]
+    if pg:
+        t = torch.tensor([ms], dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank == 0:
+        b = leg["batched"]
+        line = {"metric": "batched graphs/s", "value": world * count / (ms / 1e3), "unit": "graphs/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic",
+                "config": {"workload": leg["workload"], "graphs": count, "m_input": leg["m_input"],
+                           "m_hat": leg["m_hat"], "packs": leg["packs"],
+                           "l2": "inputs larger than L2 (edge lists and lists exceed 129 MB)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": None, "cpu_baseline": None,
+                "e2e": {"value": world * count / (b["e2e_ms"] / 1e3), "unit": "graphs/s",
+                        "h2d_bytes_per_step": 8 * leg["m_input"], "d2h_bytes_per_step": 8 * count},
+                "gpu_launches": b["gpu_launches_per_step"] * args.steps, "clocks": clk, "batch": leg}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
 def run_gpu(args, rank, world, local):
     import numpy as np
     import torch
     import paper_1406_5687_gb300 as tc
     from graphgen import workloads as W
 
+    if args.workload == "batch":
+        return run_batch_only(args, rank, world, local)
     torch.cuda.set_device(local)
     pg = None
     if world > 1:
@@ -359,6 +585,10 @@ def run_gpu(args, rank, world, local):
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, CPU_SAMPLE_PAIRS[args.workload])
 
+    batch = None
+    if rank == 0 and not args.no_batch:
+        batch = batch_leg(args.batch_graphs or 512, max(2, min(args.steps, 3)), args.warmup)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -376,7 +606,8 @@ def run_gpu(args, rank, world, local):
                 "count_only": {"value": m_hat / (count_ms / 1e3), "unit": UNIT,
                                "note": "m_hat / (cost prefix + schedule + intersection), lists resident"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "work": {"small": alg["small"], "big": alg["big"]}, "wall_s_timed": t_wall}
+                "clocks": clk, "work": {"small": alg["small"], "big": alg["big"]}, "wall_s_timed": t_wall,
+                "batch": batch}
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()

@@ -300,38 +300,112 @@ tc_status tc_count_static(tc_graph_t g, tc_stream_t stream, uint64_t* total_dev)
 
 /* ------------------------------------------------------------------ batch */
 
+/*
+ * Batched counting.  The paper counts one graph at a time; counting many independent graphs
+ * in one pass is this library's own addition.  k graphs are packed, as disjoint unions with
+ * each graph's vertex ids moved into a range of their own, into as few packs as the limits
+ * allow: at most pack_edges input edges and 2^30 vertices per pack, a graph with more edges
+ * than pack_edges forming a pack of its own.  Each pack goes once through the single-graph
+ * build (steps a1-a5 and the task decomposition), so a pack's sort, degree, orientation and
+ * list kernels serve all of its graphs.  Degrees, the order of Sec. III-A and every list are
+ * those of each graph alone: the union has no edge between graphs.
+ */
 typedef struct tc_batch* tc_batch_t;
 
 /*
- * Batched counting: k built graphs counted by one persistent launch.  Their task
- * arrays are addressed through a device table of per-graph descriptors with
- * int64 offsets; one global chunk schedule (Eq. 1 + Eq. 2) spans every graph's
- * tasks, and each chunk adds into its own graph's total.  The launch sequence is
- * captured once into a CUDA graph and replayed by tc_batch_run.
- *   graphs  host array of k handles (kept referenced, not owned: free the batch
- *           before any of its graphs).
+ * Build a batch.
+ *   src, dst    host arrays of k pointers: graph j's edges are src[j][0..m[j]) and
+ *               dst[j][0..m[j]) (int32, host or device memory, never modified).
+ *   m, n        host arrays of k sizes, m[j] >= 0, 0 <= n[j] <= 2^30.
+ *   pack_edges  input edges per pack at most (0 = 2^30).
+ *   opt         NULL = defaults; input policy, hub threshold (small_max) and count options
+ *               of every graph.
+ *   out         receives the batch (free with tc_batch_free).
+ * Errors: TC_ERR_INVALID_ARG; TC_ERR_VERTEX_RANGE (an id outside [0, n[j]) in graph j);
+ * TC_ERR_OOM / TC_ERR_BUDGET; TC_ERR_UNSUPPORTED (a graph beyond the single-graph limits).
+ * Synchronises `stream`.
  */
-tc_status tc_batch_create(const tc_graph_t* graphs, int32_t k, const tc_options* opt,
-                          tc_stream_t stream, tc_batch_t* out);
-
-/* Replay the captured launch; totals_dev: device, k uint64 (overwritten). */
-tc_status tc_batch_run(tc_batch_t b, tc_stream_t stream, uint64_t* totals_dev);
-
-void tc_batch_free(tc_batch_t b);
-
-/* Convenience: create, run once, copy the k totals to host memory, free. */
-tc_status tc_batch_count(const tc_graph_t* graphs, int32_t k, tc_stream_t stream, uint64_t* totals);
+tc_status tc_batch_build(const int32_t* const* src, const int32_t* const* dst, const int64_t* m,
+                         const int32_t* n, int32_t k, int64_t pack_edges, const tc_options* opt,
+                         tc_stream_t stream, tc_batch_t* out);
 
 /*
- * Batched build: k edge lists (host memory) built into k handles through one
- * packed pipeline (one sort over graph-tagged keys).
- *   src, dst   host arrays of k pointers to int32 edge arrays (host memory).
- *   m, n       host arrays of k sizes.
- *   out        host array of k handles (each freed with tc_free).
+ * Count every graph of the batch.  Per pack: the task costs and their prefix (step a6),
+ * one Eq. 1 + Eq. 2 schedule over all of the pack's tasks, and one launch of each count
+ * kernel, whose chunks are cut at graph boundaries so that each graph's hits go to its own
+ * total.  The launches of all packs are captured into one CUDA graph on the first run (and
+ * again after tc_batch_set_options) and replayed.
+ *   totals_dev  device, k uint64, overwritten: graph j's exact triangle count at index j.
+ * Enqueue only: check errors with tc_batch_check.  Runs of one batch must not overlap on
+ * the device (they share its work buffers).
  */
-tc_status tc_build_batch(const int32_t* const* src, const int32_t* const* dst, const int64_t* m,
-                         const int32_t* n, int32_t k, const tc_options* opt, tc_stream_t stream,
-                         tc_graph_t* out);
+tc_status tc_batch_run(tc_batch_t b, tc_stream_t stream, uint64_t* totals_dev);
+
+/* Synchronise `stream`; return (and clear) the first device error of any pack. */
+tc_status tc_batch_check(tc_batch_t b, tc_stream_t stream);
+
+/* tc_batch_run, then copy the k totals to host memory `totals` and check. */
+tc_status tc_batch_count(tc_batch_t b, tc_stream_t stream, uint64_t* totals);
+
+typedef struct tc_batch_info {
+    int32_t k;             /* graphs */
+    int32_t packs;
+    int32_t max_dhat;      /* longest N+ list of any graph */
+    int32_t reserved;
+    int64_t m_in;          /* input edges, all graphs */
+    int64_t m_hat;         /* distinct edges, all graphs */
+    int64_t tasks;
+    int64_t tasks_small;
+    int64_t device_bytes;  /* device memory held by the batch */
+} tc_batch_info;
+
+tc_status tc_batch_get_info(tc_batch_t b, tc_batch_info* info);
+
+/* Each graph's distinct edge count m_hat[j] (host, k int64). */
+tc_status tc_batch_graph_edges(tc_batch_t b, int64_t* m_hat);
+
+/*
+ * Replace the count-time options (piece, warps_per_block, big_warps, blocks_per_sm,
+ * static_percent, min_chunk, c_task, c_owner, cost_model, retry_limit).  The build-time
+ * fields (input_policy, small_max, allocator hooks, budget) must equal the build's:
+ * TC_ERR_INVALID_ARG otherwise.  Waits for the batch's last stream.
+ */
+tc_status tc_batch_set_options(tc_batch_t b, const tc_options* opt);
+
+/* Release the batch (NULL-safe; waits for its last stream). */
+void tc_batch_free(tc_batch_t b);
+
+/*
+ * Autotuner for the batched count.  The given graphs (a sample of a workload) are built as a
+ * batch once per hub threshold small_max in {32, 64, 128}, and each build is counted with
+ * every launch shape warps_per_block in {4, 8, 16} (small-owner kernel) x big_warps in
+ * {8, 16} x piece in {1024, 2048} (big-owner table of 8 x piece slots).  Each candidate is
+ * timed with CUDA events on `stream` and keeps the fastest of `reps` runs after one warm-up.
+ *   opt     base options (NULL = defaults); the other fields are kept.
+ *   best    receives the fastest candidate's options.
+ *   report  optional: entries[0..cap) receive the candidates in the order tried; n, the
+ *           fastest time and the time of the base options' own shape (-1 if not in the grid).
+ */
+typedef struct tc_tune_entry {
+    int32_t small_max;
+    int32_t warps_per_block;
+    int32_t big_warps;
+    int32_t piece;
+    int32_t static_percent;
+    float ms;
+} tc_tune_entry;
+
+typedef struct tc_tune_report {
+    tc_tune_entry* entries;
+    int32_t cap;
+    int32_t n;
+    float best_ms;
+    float default_ms;
+} tc_tune_report;
+
+tc_status tc_batch_autotune(const int32_t* const* src, const int32_t* const* dst, const int64_t* m,
+                            const int32_t* n, int32_t k, const tc_options* opt, int32_t reps,
+                            tc_stream_t stream, tc_options* best, tc_tune_report* report);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -16,7 +16,7 @@ from ._lib import (TC_COST_DEGREE, TC_COST_EDGE, TC_COST_MERGE, TC_COST_NEW, TC_
                    TC_FN_DEGREE, TC_FN_NEW, TC_FN_ONE, TC_FN_PATRIC, TC_INPUT_SANITIZE, TC_INPUT_STRICT, TcError,
                    default_options)
 
-__all__ = ["Graph", "Batch", "Server", "TcError", "default_options", "load", "version", "kernel_launches"]
+__all__ = ["Graph", "Batch", "autotune", "Server", "TcError", "default_options", "load", "version", "kernel_launches"]
 
 
 def load():
@@ -238,5 +238,5 @@ class Graph:
         return deg, off, cols, tasks
 
 
-from .batch import Batch  # noqa: E402
+from .batch import Batch, autotune  # noqa: E402
 from .server import Server  # noqa: E402

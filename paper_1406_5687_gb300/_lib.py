@@ -64,6 +64,25 @@ class CountTrace(ctypes.Structure):
                 ("kernel_small_ms", ctypes.c_float), ("kernel_big_ms", ctypes.c_float), ("reserved", ctypes.c_float)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("packs", ctypes.c_int32), ("max_dhat", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("m_in", ctypes.c_int64), ("m_hat", ctypes.c_int64),
+                ("tasks", ctypes.c_int64), ("tasks_small", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("small_max", ctypes.c_int32), ("warps_per_block", ctypes.c_int32), ("big_warps", ctypes.c_int32),
+                ("piece", ctypes.c_int32), ("static_percent", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("entries", ctypes.POINTER(TuneEntry)), ("cap", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float)]
+
+
 class Result(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_uint64), ("total", ctypes.c_uint64), ("status", ctypes.c_int32),
                 ("slot", ctypes.c_int32), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
@@ -91,11 +110,17 @@ SIGNATURES = {
                                    ctypes.POINTER(CountTrace)]),
     "tc_kernel_launches": (ctypes.c_int64, []),
     "tc_count_static": (ctypes.c_int, [P, P, P]),
-    "tc_batch_create": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(Options), P, ctypes.POINTER(P)]),
+    "tc_batch_build": (ctypes.c_int, [P, P, P, P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(Options), P,
+                                      ctypes.POINTER(P)]),
     "tc_batch_run": (ctypes.c_int, [P, P, P]),
+    "tc_batch_check": (ctypes.c_int, [P, P]),
+    "tc_batch_count": (ctypes.c_int, [P, P, P]),
+    "tc_batch_get_info": (ctypes.c_int, [P, ctypes.POINTER(BatchInfo)]),
+    "tc_batch_graph_edges": (ctypes.c_int, [P, P]),
+    "tc_batch_set_options": (ctypes.c_int, [P, ctypes.POINTER(Options)]),
     "tc_batch_free": (None, [P]),
-    "tc_batch_count": (ctypes.c_int, [P, ctypes.c_int32, P, P]),
-    "tc_build_batch": (ctypes.c_int, [P, P, P, P, ctypes.c_int32, ctypes.POINTER(Options), P, P]),
+    "tc_batch_autotune": (ctypes.c_int, [P, P, P, P, ctypes.c_int32, ctypes.POINTER(Options), ctypes.c_int32, P,
+                                         ctypes.POINTER(Options), ctypes.POINTER(TuneReport)]),
     "tc_server_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Options), ctypes.POINTER(P)]),
     "tc_server_submit": (ctypes.c_int, [P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64]),
     "tc_server_poll": (ctypes.c_int, [P, ctypes.POINTER(Result), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),

@@ -63,7 +63,7 @@ int64_t graph_resident_bytes(int64_t m_hat, int64_t tasks, int32_t n) {
            8 * (tasks / 2048 + 64) + 8 * (int64_t)n + (1 << 16);
 }
 
-static void free_graph(tc_graph* g) {
+void free_graph(tc_graph* g) {
     if (!g) return;
     cudaStream_t s = g->last_stream;
     cudaStreamSynchronize(s);
@@ -78,12 +78,44 @@ static void free_graph(tc_graph* g) {
     put(g->work.prefix, (size_t)(g->tasks + 1) * 8);
     put(g->work.scan_scr, (size_t)g->work.scan_words * 8);
     put(g->work.fcost, (size_t)(g->n > 0 ? g->n : 1) * 8);
+    put(g->sub_task, (size_t)(g->n_sub > 0 ? 2 * ((size_t)g->n_sub + 1) : 0) * 8);
     put(g->status, sizeof(HandleDev));
     cudaStreamSynchronize(s);
     delete g;
 }
 
-static tc_status read_status(tc_graph* g, cudaStream_t s, unsigned long long* result) {
+// A new empty handle with its device status block, on stream s (options already checked).
+tc_status new_graph(const tc_options& o, cudaStream_t s, tc_graph** out) {
+    *out = nullptr;
+    retain_pool_memory();
+    tc_graph* g = new (std::nothrow) tc_graph();
+    if (!g) return TC_ERR_OOM;
+    g->opt = o;
+    g->al.alloc = o.alloc;
+    g->al.release = o.release;
+    g->al.ctx = o.alloc_ctx;
+    g->al.budget = o.hbm_budget_bytes;
+    g->last_stream = s;
+    cudaGetDevice(&g->device);
+    void* p = nullptr;
+    tc_status st = g->al.get(&p, sizeof(HandleDev), s);
+    if (st == TC_OK) {
+        g->status = (DevStatus*)p;
+        HandleDev* hd = (HandleDev*)p;
+        g->work.result = &hd->result;
+        g->work.sched = hd->sched;
+        if (cudaMemsetAsync(p, 0, sizeof(HandleDev), s) != cudaSuccess) st = TC_ERR_CUDA;
+    }
+    if (st != TC_OK) {
+        (void)cudaGetLastError();
+        free_graph(g);
+        return st;
+    }
+    *out = g;
+    return TC_OK;
+}
+
+tc_status read_status(tc_graph* g, cudaStream_t s, unsigned long long* result) {
     HandleDev h;
     TC_CUDA_TRY(cudaMemcpyAsync(&h, g->status, offsetof(HandleDev, pad), cudaMemcpyDeviceToHost, s));
     TC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -152,29 +184,10 @@ tc_status tc_build(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
     if (mixed) return TC_ERR_INVALID_ARG;
     if (o.hbm_budget_bytes > 0 && build_peak_bytes(m, n, !dev_in) > o.hbm_budget_bytes) return TC_ERR_BUDGET;
 
-    retain_pool_memory();
-    tc_graph* g = new (std::nothrow) tc_graph();
-    if (!g) return TC_ERR_OOM;
-    g->opt = o;
-    g->al.alloc = o.alloc;
-    g->al.release = o.release;
-    g->al.ctx = o.alloc_ctx;
-    g->al.budget = o.hbm_budget_bytes;
-    g->last_stream = s;
-    cudaGetDevice(&g->device);
+    tc_graph* g = nullptr;
+    TC_TRY(new_graph(o, s, &g));
     tc_status st = TC_OK;
     {
-        void* p = nullptr;
-        st = g->al.get(&p, sizeof(HandleDev), s);
-        if (st == TC_OK) {
-            g->status = (DevStatus*)p;
-            HandleDev* hd = (HandleDev*)p;
-            g->work.result = &hd->result;
-            g->work.sched = hd->sched;
-            if (cudaMemsetAsync(p, 0, sizeof(HandleDev), s) != cudaSuccess) st = TC_ERR_CUDA;
-        }
-    }
-    if (st == TC_OK) {
         const int32_t* s_d = src;
         const int32_t* d_d = dst;
         DevBuf<int32_t> ss, dd;

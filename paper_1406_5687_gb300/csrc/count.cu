@@ -62,6 +62,8 @@ struct CountArgs {
     long long retry_limit;
     const uint32_t* own_first;  // big class: first task of each owner, then T
     long long n_owners;         // big class: owners
+    const int64_t* gtask;       // packs: this class's first task of each graph, then its end
+    long long n_sub;            // packs: graphs (0: one graph, one total)
 };
 
 // First index q in [lo, hi] with pred(q), for pred false..false true..true and pred(hi) true.
@@ -695,6 +697,39 @@ __device__ __forceinline__ void block_worker(const CountArgs& a, Process process
     }
 }
 
+// Packs: count the chunk [t0, t1) one graph at a time, adding each graph's hits into its own
+// total.  With one graph the chunk is processed as it is.  Packs count totals only, so the
+// per-vertex / per-edge instantiations (EXTRA) leave the split out.
+template <bool EXTRA, class Process>
+__device__ __forceinline__ void by_graph(const CountArgs& a, long long t0, long long t1, Process process,
+                                         unsigned long long& acc, int lane, int warp) {
+    if (EXTRA || a.n_sub == 0) {
+        process(t0, t1);
+        return;
+    }
+    __shared__ long long s_g;
+    if (warp == 0) {
+        const int64_t* __restrict__ gt = a.gtask;
+        const long long K = a.n_sub;
+        // the graph holding task t0: the first graph whose tasks end after t0
+        const long long gq = warp_first_true(0, K - 1, [&](long long q) { return q >= K - 1 || gt[q + 1] > t0; }, lane);
+        if (lane == 0) s_g = gq;
+    }
+    __syncthreads();
+    long long g = s_g;
+    for (long long t = t0; t < t1; ++g) {
+        const long long ge = a.gtask[g + 1];
+        const long long te = ge < t1 ? ge : t1;
+        if (te > t) {
+            process(t, te);
+            const unsigned long long v = warp_sum(acc);
+            if (lane == 0 && v) atomicAdd(&a.total[g], v);
+            acc = 0;
+        }
+        t = te;
+    }
+}
+
 template <bool EXTRA>
 __device__ __forceinline__ void worker_epilogue(const CountArgs& a, unsigned long long acc, int lane, long long busy,
                                                 long long nch) {
@@ -715,8 +750,10 @@ __global__ void __launch_bounds__(512, 2) k_count_small(CountArgs a) {
     uint32_t* tbl = smem_tbl + (size_t)warp * a.table_slots;
     unsigned long long acc = 0;
     long long busy = 0, nch = 0;
-    block_worker(a, [&](long long t0, long long t1) { process_small_block<EXTRA>(a, t0, t1, tbl, &s_claim, lane, acc); },
-                 lane, warp, busy, nch);
+    block_worker(a, [&](long long t0, long long t1) {
+        by_graph<EXTRA>(a, t0, t1, [&](long long u0, long long u1) { process_small_block<EXTRA>(a, u0, u1, tbl, &s_claim, lane, acc); },
+                 acc, lane, warp);
+    }, lane, warp, busy, nch);
     worker_epilogue<EXTRA>(a, acc, lane, busy, nch);
 }
 
@@ -730,7 +767,9 @@ __global__ void __launch_bounds__(512, 2) k_count_big(CountArgs a) {
     unsigned long long acc = 0;
     long long busy = 0, nch = 0;
     block_worker(a, [&](long long t0, long long t1) {
-        process_big<EXTRA>(a, t0, t1, smem_tbl, &s_win, &s_next, lane, warp, acc);
+        by_graph<EXTRA>(a, t0, t1, [&](long long u0, long long u1) {
+            process_big<EXTRA>(a, u0, u1, smem_tbl, &s_win, &s_next, lane, warp, acc);
+        }, acc, lane, warp);
     }, lane, warp, busy, nch);
     worker_epilogue<EXTRA>(a, acc, lane, busy, nch);
 }
@@ -877,9 +916,10 @@ static tc_status grid_for_kernel(K kernel, int threads, size_t smem, int cap_per
 
 tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsigned long long* total_dev,
                         unsigned long long* t_v, uint32_t* per_edge, tc_count_trace* trace) {
+    const bool extra = t_v != nullptr || per_edge != nullptr;
+    if (g->n_sub > 0 && (extra || trace)) return TC_ERR_UNSUPPORTED;
     TC_TRY(ensure_count_work(g, opt, s));
     CountWork& w = g->work;
-    const bool extra = t_v != nullptr || per_edge != nullptr;
     const long long T = g->tasks, Ts = g->tasks_small;
     // small class: blocks whose warps each have a table
     const int wpb = opt.warps_per_block;
@@ -915,7 +955,7 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     k_sched_init<<<1, 1, 0, s>>>(w.sched, w.prefix, Ts, T, W_s, W_b, opt.static_percent, opt.min_chunk);
     note_launch();
     TC_CUDA_TRY(cudaGetLastError());
-    TC_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(unsigned long long), s));
+    TC_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(unsigned long long) * (g->n_sub > 0 ? g->n_sub : 1), s));
     if (t_v && g->n > 0) TC_CUDA_TRY(cudaMemsetAsync(t_v, 0, sizeof(unsigned long long) * g->n, s));
     if (per_edge && g->m_hat > 0) TC_CUDA_TRY(cudaMemsetAsync(per_edge, 0, sizeof(uint32_t) * g->m_hat, s));
     if (trace) TC_CUDA_TRY(cudaEventRecord(ev[1], s));
@@ -937,7 +977,9 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     a.retry_limit = opt.retry_limit > 0 ? opt.retry_limit : (1ll << 24);
     a.own_first = g->own_first;
     a.n_owners = g->owners_big;
+    a.n_sub = g->n_sub;
     // small class
+    a.gtask = g->sub_task;
     a.t_begin = 0;
     a.t_end = Ts;
     a.sched = w.sched;
@@ -955,6 +997,7 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     }
     if (trace) TC_CUDA_TRY(cudaEventRecord(ev[2], s));
     // big class
+    a.gtask = g->sub_task ? g->sub_task + (g->n_sub + 1) : nullptr;
     a.t_begin = Ts;
     a.t_end = T;
     a.sched = w.sched + 1;
@@ -1080,6 +1123,8 @@ static tc_status count_enqueue_static(tc_graph* g, cudaStream_t s, unsigned long
     a.retry_limit = opt.retry_limit > 0 ? opt.retry_limit : (1ll << 24);
     a.own_first = g->own_first;
     a.n_owners = g->owners_big;
+    a.gtask = nullptr;
+    a.n_sub = 0;
     a.t_begin = 0;
     a.t_end = Ts;
     a.sched = sched;

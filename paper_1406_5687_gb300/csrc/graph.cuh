@@ -73,6 +73,11 @@ struct tc_graph {
     tcg::DevStatus* status = nullptr;
     tcg::CountWork work;
     int64_t bytes = 0;             // device bytes held
+    // A pack (batched counting): the handle holds n_sub graphs as one disjoint union, graph j's
+    // vertex v being vertex vbase[j] + v.  sub_task (device, 2 (n_sub + 1)) holds, per task
+    // class, the first task of each graph and then the class's end; a count writes n_sub totals.
+    int32_t n_sub = 0;
+    int64_t* sub_task = nullptr;
     cudaStream_t last_stream = nullptr;  // stream of the last call; tc_free waits for it
 };
 
@@ -95,6 +100,16 @@ tc_status build_graph(tc_graph* g, const int32_t* src_d, const int32_t* dst_d, i
                       cudaStream_t s);
 
 tc_status check_options(const tc_options& o);
+
+// Handle life cycle (api.cu): an empty handle with its status block; release everything;
+// read (and clear) the device error word after synchronising s, optionally the last total.
+tc_status new_graph(const tc_options& o, cudaStream_t s, tc_graph** out);
+void free_graph(tc_graph* g);
+tc_status read_status(tc_graph* g, cudaStream_t s, unsigned long long* result);
+
+// Device bytes a build of (m, n) holds at its peak, and a built graph keeps (api.cu).
+int64_t build_peak_bytes(int64_t m, int32_t n, bool host_input);
+int64_t graph_resident_bytes(int64_t m_hat, int64_t tasks, int32_t n);
 
 // Slots of one small-class warp table: room for one owner of small_max entries at a load of
 // at most 1/8, and at least 1024 so that a window of tiny owners fits at once.  Region
