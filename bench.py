@@ -43,6 +43,7 @@ CPU_SAMPLE_PAIRS = {"cl": 32_000_000, "ba": 16_000_000, "er": 100_000, "cl_small
 # input pairs per step of the reference (oracle) arm, so that --steps K --warmup W ends in minutes
 REF_SAMPLE_PAIRS = {"cl": 4_000_000, "ba": 2_000_000, "er": 100_000, "cl_small": 2_000_000}
 REF_BATCH_GRAPHS = 8
+REF_SERVE_GRAPHS = 2
 
 
 def parse_args():
@@ -50,11 +51,17 @@ def parse_args():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--workload", default="cl", choices=["cl", "ba", "er", "cl_small", "batch"])
+    p.add_argument("--workload", default="cl", choices=["cl", "ba", "er", "cl_small", "batch", "serve"])
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain leg")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving-vs-plain leg")
+    p.add_argument("--serve-requests", type=int, default=0,
+                   help="requests of the serving window (default: 256 as a leg of a single-graph run, 2000 "
+                        "with --workload serve)")
+    p.add_argument("--serve-pool", type=int, default=0,
+                   help="pre-generated graphs the requests cycle through (default 32, or 256 with --workload serve)")
     p.add_argument("--batch-graphs", type=int, default=0,
                    help="graphs of the batched workload (default: 512 as a leg of a single-graph run, "
                         "4096 with --workload batch)")
@@ -353,14 +360,122 @@ def batch_leg(count, steps, warmup, tune_sample=64, oracle_sample=4):
     }
 
 
+# --------------------------------------------------------------------------- serving and plain
+
+SERVE_TEXT = ("serving: Poisson arrivals at 2,000 graphs/s of Chung-Lu graphs, seed 4 (exponent uniform in "
+              "[2.1, 2.8], n log-uniform in [1e4, 2e6], average degree uniform in [16, 96]), a finite window of "
+              "requests cycling through a pool of pre-generated graphs in pinned host memory, 60 GB budget")
+SERVE_RATE = 2000.0
+SERVE_BUDGET = 60 << 30
+
+
+def serve_pool(count):
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    from graphgen import workloads as W
+
+    def gen(j):
+        sp = W.serve_spec(j)
+        s, d = sp.edges()
+        return torch.from_numpy(s).pin_memory(), torch.from_numpy(d).pin_memory(), sp.n
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        return list(ex.map(gen, range(count)))
+
+
+def _pct(x, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(x), q)) * 1e3
+
+
+def serve_leg(requests, pool_size, slots=4):
+    """The server (continuous batching, `slots` slot threads, 60 GB budget) against a
+    one-at-a-time loop of tc_build + tc_count + tc_free, on the same Poisson arrival trace."""
+    import numpy as np
+    import torch
+    import paper_1406_5687_gb300 as tc
+    from graphgen import workloads as W
+    t0 = time.perf_counter()
+    pool = serve_pool(pool_size)
+    gen_s = time.perf_counter() - t0
+    arrivals = W.poisson_arrivals(requests, SERVE_RATE)
+    pick = [i % pool_size for i in range(requests)]
+    edges_in = sum(int(pool[j][0].numel()) for j in pick)
+
+    with tc.Server(SERVE_BUDGET, slots=slots) as sv:
+        for j in range(min(4, pool_size)):  # warm-up
+            sv.submit(*pool[j], tag=-1)
+        sv.drain(-1)
+        sv.poll(16)
+        l0 = tc.kernel_launches()
+        start = time.perf_counter()
+        for i in range(requests):
+            delay = start + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            sv.submit(*pool[pick[i]], tag=i)
+        sv.drain(-1)
+        res = sorted(sv.poll(requests + 16), key=lambda r: r["tag"])
+        launches = tc.kernel_launches() - l0
+        st = sv.stats()
+    if len(res) != requests or any(r["status"] != 0 for r in res):
+        raise RuntimeError("serving lost or failed requests")
+    s_lat = [r["t_done"] - r["t_submit"] for r in res]
+    s_span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+    s_tot = [r["total"] for r in res]
+
+    # plain: one request at a time on the same arrival trace
+    stream = torch.cuda.current_stream()
+    p_lat, p_tot = [], []
+    for j in range(min(4, pool_size)):
+        g = tc.Graph.build(*pool[j][:2], pool[j][2], stream=stream)
+        g.count(stream)
+        g.free()
+    start = time.perf_counter()
+    for i in range(requests):
+        arrive = start + arrivals[i]
+        delay = arrive - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        s_, d_, n_ = pool[pick[i]]
+        g = tc.Graph.build(s_, d_, n_, stream=stream)
+        p_tot.append(g.count(stream))
+        g.free()
+        p_lat.append(time.perf_counter() - arrive)
+    p_span = time.perf_counter() - start
+    if p_tot != s_tot:
+        raise RuntimeError("served totals differ from the plain path")
+    import oracle
+    for j in range(min(2, pool_size)):
+        s_, d_, n_ = pool[j]
+        if oracle.count_edges(n_, s_.numpy(), d_.numpy()) != s_tot[j]:
+            raise RuntimeError(f"request {j}: served total differs from the oracle")
+    return {
+        "workload": SERVE_TEXT, "requests": requests, "pool_graphs": pool_size, "edges_in": edges_in,
+        "offered_graphs_per_s": SERVE_RATE, "slots": slots, "unit": "graphs/s",
+        "served": {"graphs_per_s": requests / s_span, "edges_per_s": edges_in / s_span,
+                   "p50_ms": _pct(s_lat, 50), "p99_ms": _pct(s_lat, 99), "span_s": s_span,
+                   "groups": st["groups"], "grouped_requests": st["grouped"],
+                   "peak_bytes_in_flight": st["peak_bytes_in_flight"], "peak_slots_busy": st["peak_slots_busy"],
+                   "gpu_launches": launches},
+        "plain": {"graphs_per_s": requests / p_span, "edges_per_s": edges_in / p_span,
+                  "p50_ms": _pct(p_lat, 50), "p99_ms": _pct(p_lat, 99), "span_s": p_span},
+        "p99_vs_plain": _pct(s_lat, 99) / _pct(p_lat, 99),
+        "throughput_vs_plain": p_span / s_span,
+        "oracle_checked_requests": list(range(min(2, pool_size))), "generate_s": gen_s,
+        "latency": "arrival (submit) to result on the host, steady clock",
+    }
+
+
 # --------------------------------------------------------------------------- reference arm
 
 def run_reference_batch(args):
-    """The oracle, graph by graph, on the first graphs of the batched workload (a bounded
-    sample per step): graphs/s on the host."""
+    """The oracle, graph by graph, on the first graphs of the batched (or served) workload, a
+    bounded sample per step: graphs/s on the host."""
     import oracle
     from graphgen import workloads as W
-    specs = W.batch_specs(REF_BATCH_GRAPHS)
+    serve = args.workload == "serve"
+    specs = [W.serve_spec(j) for j in range(REF_SERVE_GRAPHS)] if serve else W.batch_specs(REF_BATCH_GRAPHS)
     graphs = [(sp.n,) + sp.edges() for sp in specs]
     times = []
     for i in range(args.warmup + args.steps):
@@ -371,13 +486,15 @@ def run_reference_batch(args):
             times.append(time.perf_counter() - t0)
     mean = sum(times) / len(times)
     value = len(graphs) / mean
-    line = {"impl": "reference", "metric": "batched graphs/s", "value": value, "unit": "graphs/s",
+    line = {"impl": "reference", "metric": "served graphs/s" if serve else "batched graphs/s", "value": value,
+            "unit": "graphs/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": BATCH_TEXT, "graphs": len(graphs)},
+            "config": {"workload": SERVE_TEXT if serve else BATCH_TEXT, "graphs": len(graphs)},
             "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {len(graphs)} graphs of the batched workload per step, oracle end to "
-                                       "end, one graph after another, single thread"},
+                             "sample": f"first {len(graphs)} graphs of the {'served' if serve else 'batched'} "
+                                       "workload per step, oracle end to end, one graph after another, "
+                                       "single thread"},
             "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -386,7 +503,7 @@ def run_reference_batch(args):
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    if args.workload == "batch":
+    if args.workload in ("batch", "serve"):
         return run_reference_batch(args)
     import oracle
     from graphgen import workloads as W
@@ -464,6 +581,32 @@ def run_batch_only(args, rank, world, local):
     return 0
 
 
+def run_serve_only(args, rank, world, local):
+    """--workload serve: the serving leg alone at its full window, as the JSON line's metric."""
+    import torch
+    torch.cuda.set_device(local)
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get(
+        "CUDA_VISIBLE_DEVICES") else str(local)
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    leg = serve_leg(args.serve_requests or 2000, args.serve_pool or 256)
+    clk = clocks.stop()
+    if rank == 0:
+        sv = leg["served"]
+        line = {"metric": "served graphs/s", "value": world * sv["graphs_per_s"], "unit": "graphs/s",
+                "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": sv["span_s"] * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic",
+                "config": {"workload": leg["workload"], "requests": leg["requests"], "pool": leg["pool_graphs"],
+                           "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": None, "cpu_baseline": None,
+                "e2e": {"value": world * sv["graphs_per_s"], "unit": "graphs/s",
+                        "h2d_bytes_per_step": 8 * leg["edges_in"], "d2h_bytes_per_step": 8 * leg["requests"]},
+                "gpu_launches": sv["gpu_launches"], "clocks": clk, "serve": leg}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gpu(args, rank, world, local):
     import numpy as np
     import torch
@@ -472,6 +615,8 @@ def run_gpu(args, rank, world, local):
 
     if args.workload == "batch":
         return run_batch_only(args, rank, world, local)
+    if args.workload == "serve":
+        return run_serve_only(args, rank, world, local)
     torch.cuda.set_device(local)
     pg = None
     if world > 1:
@@ -588,6 +733,9 @@ def run_gpu(args, rank, world, local):
     batch = None
     if rank == 0 and not args.no_batch:
         batch = batch_leg(args.batch_graphs or 512, max(2, min(args.steps, 3)), args.warmup)
+    serve = None
+    if rank == 0 and not args.no_serve:
+        serve = serve_leg(args.serve_requests or 256, args.serve_pool or 32)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -607,7 +755,7 @@ def run_gpu(args, rank, world, local):
                                "note": "m_hat / (cost prefix + schedule + intersection), lists resident"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "work": {"small": alg["small"], "big": alg["big"]}, "wall_s_timed": t_wall,
-                "batch": batch}
+                "batch": batch, "serve": serve}
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()

@@ -409,48 +409,77 @@ tc_status tc_batch_autotune(const int32_t* const* src, const int32_t* const* dst
 
 /* ---------------------------------------------------------------- serving */
 
+/*
+ * Serving with continuous batching (this library's own addition; the paper counts one
+ * graph at a time).  Submitted graphs wait in a FIFO host queue.  Each of `slots` slot
+ * threads owns a CUDA stream; whenever a slot is free it takes the requests at the head of
+ * the queue -- as many as fit within group_edges input edges and within what is left of the
+ * device-memory budget -- and counts them: one request through the single-graph path
+ * (tc_build + tc_count), several as one batch (tc_batch_build + tc_batch_count, one pack).
+ * Requests that arrive while others run are admitted as soon as a slot and memory free up,
+ * and the work of different slots overlaps on the device.  A request's device memory
+ * (its CSR, tasks and build scratch) is held from admission until its result has been read
+ * back, then released.  Every total is exact and the same as the graph's count alone.
+ */
 typedef struct tc_server* tc_server_t;
 
 typedef struct tc_result {
     uint64_t tag;       /* the caller's tag from tc_server_submit */
-    uint64_t total;     /* T */
+    uint64_t total;     /* T (0 if status != TC_OK) */
     int32_t status;     /* tc_status of this request */
-    int32_t slot;       /* the execution slot that ran it */
-    double t_submit;    /* seconds (steady clock) when submitted */
-    double t_start;     /* when admitted to a slot */
-    double t_done;      /* when the result was known on the host */
+    int32_t slot;       /* the slot that ran it */
+    int32_t group;      /* requests counted together with it, itself included */
+    int32_t reserved;
+    double t_submit;    /* seconds on the steady clock when submitted */
+    double t_start;     /* when a slot admitted it */
+    double t_done;      /* when its result was known on the host */
 } tc_result;
 
 /*
- * A request loop with continuous batching: submitted edge lists wait in a host
- * queue; a scheduler thread admits them to one of `slots` execution slots (each
- * with its own CUDA stream) as soon as a slot is free and the device memory of
- * the requests in flight stays within hbm_budget_bytes; builds and counts of
- * different slots overlap on the device.  The CSR of a finished request is
- * released as soon as its result is read back.
- *   hbm_budget_bytes  > 0.
- *   slots             1..64.
- *   opt               NULL = defaults.
+ * Create a server on the current device.
+ *   hbm_budget_bytes  > 0: device memory the requests in flight may hold together, by the
+ *                     library's estimate of each build's peak.
+ *   slots             1..64 slot threads (and streams).
+ *   group_edges       input edges one slot takes at once at most (0 = 2^26; 1 = every
+ *                     request alone).
+ *   opt               NULL = defaults; options of every request.
  */
-tc_status tc_server_create(int64_t hbm_budget_bytes, int32_t slots, const tc_options* opt,
-                           tc_server_t* out);
+tc_status tc_server_create(int64_t hbm_budget_bytes, int32_t slots, int64_t group_edges,
+                           const tc_options* opt, tc_server_t* out);
 
 /*
- * Queue one graph.  src/dst: host, m int32 each; the server copies them before
- * returning, so the caller may reuse them.  Errors: TC_ERR_INVALID_ARG,
- * TC_ERR_BUDGET (the graph alone needs more than the budget), TC_ERR_OOM.
+ * Queue one graph.  src/dst: m int32 each, host (pinned for full copy speed) or device
+ * memory.  The server BORROWS them: they must stay valid and unchanged until this request's
+ * result has been returned by tc_server_poll.  tag: any value, returned with the result.
+ * Errors: TC_ERR_INVALID_ARG; TC_ERR_BUDGET (the graph alone needs more than the budget).
+ * A graph's own errors (e.g. TC_ERR_VERTEX_RANGE) come back in its result.
  */
 tc_status tc_server_submit(tc_server_t s, const int32_t* src, const int32_t* dst, int64_t m,
                            int32_t n, uint64_t tag);
 
-/* Move up to max finished results into out (host); *n_out receives how many. */
+/* Move up to max finished results into out (host, oldest first); *n_out: how many. */
 tc_status tc_server_poll(tc_server_t s, tc_result* out, int32_t max, int32_t* n_out);
 
-/* Block until every submitted request has finished or timeout_ms passes
- * (TC_ERR_TIMEOUT). */
+/* Block until every submitted request has a result, or timeout_ms passes (TC_ERR_TIMEOUT;
+ * timeout_ms < 0 waits without limit). */
 tc_status tc_server_drain(tc_server_t s, int64_t timeout_ms);
 
-/* Stop the scheduler, wait for in-flight work, release everything (NULL-safe). */
+typedef struct tc_server_stats {
+    int64_t submitted;
+    int64_t finished;      /* results produced (polled or not) */
+    int64_t queued;        /* waiting for a slot */
+    int64_t groups;        /* slot admissions */
+    int64_t grouped;       /* requests admitted together with others */
+    int64_t bytes_in_flight;
+    int64_t peak_bytes_in_flight;  /* never above the budget */
+    int32_t peak_slots_busy;
+    int32_t reserved;
+} tc_server_stats;
+
+tc_status tc_server_get_stats(tc_server_t s, tc_server_stats* st);
+
+/* Stop taking requests, finish those in flight, drop those still queued, release
+ * everything (NULL-safe). */
 void tc_server_destroy(tc_server_t s);
 
 #ifdef __cplusplus

@@ -85,8 +85,18 @@ class TuneReport(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_uint64), ("total", ctypes.c_uint64), ("status", ctypes.c_int32),
-                ("slot", ctypes.c_int32), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
-                ("t_done", ctypes.c_double)]
+                ("slot", ctypes.c_int32), ("group", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("finished", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("groups", ctypes.c_int64), ("grouped", ctypes.c_int64), ("bytes_in_flight", ctypes.c_int64),
+                ("peak_bytes_in_flight", ctypes.c_int64), ("peak_slots_busy", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 # name -> (restype, argtypes); every function declared in include/tc.h
@@ -121,10 +131,12 @@ SIGNATURES = {
     "tc_batch_free": (None, [P]),
     "tc_batch_autotune": (ctypes.c_int, [P, P, P, P, ctypes.c_int32, ctypes.POINTER(Options), ctypes.c_int32, P,
                                          ctypes.POINTER(Options), ctypes.POINTER(TuneReport)]),
-    "tc_server_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Options), ctypes.POINTER(P)]),
+    "tc_server_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(Options),
+                                        ctypes.POINTER(P)]),
     "tc_server_submit": (ctypes.c_int, [P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64]),
     "tc_server_poll": (ctypes.c_int, [P, ctypes.POINTER(Result), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "tc_server_drain": (ctypes.c_int, [P, ctypes.c_int64]),
+    "tc_server_get_stats": (ctypes.c_int, [P, ctypes.POINTER(ServerStats)]),
     "tc_server_destroy": (None, [P]),
 }
 

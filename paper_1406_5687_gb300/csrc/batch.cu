@@ -445,17 +445,4 @@ tc_status tc_batch_autotune(const int32_t* const* src, const int32_t* const* dst
     return TC_OK;
 }
 
-// ------------------------------------------------------------------ serving (placeholder)
-
-tc_status tc_server_create(int64_t, int32_t, const tc_options*, tc_server_t* out) {
-    if (out) *out = nullptr;
-    return TC_ERR_UNSUPPORTED;
-}
-tc_status tc_server_submit(tc_server_t, const int32_t*, const int32_t*, int64_t, int32_t, uint64_t) {
-    return TC_ERR_UNSUPPORTED;
-}
-tc_status tc_server_poll(tc_server_t, tc_result*, int32_t, int32_t*) { return TC_ERR_UNSUPPORTED; }
-tc_status tc_server_drain(tc_server_t, int64_t) { return TC_ERR_UNSUPPORTED; }
-void tc_server_destroy(tc_server_t) {}
-
 }  // extern "C"

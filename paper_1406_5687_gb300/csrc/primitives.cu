@@ -32,13 +32,13 @@ void retain_pool_memory() {
 }
 
 int num_sms() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
+    // initialised once, thread-safely (slot threads of a server may ask at the same time)
+    static const int sms = [] {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
     return sms;
 }
 
