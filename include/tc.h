@@ -298,6 +298,14 @@ int64_t tc_kernel_launches(void);
 #define TC_COUNT_STATIC_MAX_TASKS (1ll << 19)
 tc_status tc_count_static(tc_graph_t g, tc_stream_t stream, uint64_t* total_dev);
 
+/*
+ * Self-test of the library's bounded device waits (the paper has no counterpart).  One
+ * thread waits, through the same wait routine the radix sort's look-back uses, on a device
+ * flag that nothing sets.  It must give up after spin_limit polls (>= 1) and return
+ * TC_ERR_TIMEOUT; the CUDA context stays usable.  Synchronises `stream`.
+ */
+tc_status tc_wait_selftest(int64_t spin_limit, tc_stream_t stream);
+
 /* ------------------------------------------------------------------ batch */
 
 /*

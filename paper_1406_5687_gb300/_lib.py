@@ -120,6 +120,7 @@ SIGNATURES = {
                                    ctypes.POINTER(CountTrace)]),
     "tc_kernel_launches": (ctypes.c_int64, []),
     "tc_count_static": (ctypes.c_int, [P, P, P]),
+    "tc_wait_selftest": (ctypes.c_int, [ctypes.c_int64, P]),
     "tc_batch_build": (ctypes.c_int, [P, P, P, P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(Options), P,
                                       ctypes.POINTER(P)]),
     "tc_batch_run": (ctypes.c_int, [P, P, P]),

@@ -6,7 +6,8 @@
 //   a4  orientation by the order of Sec. III-A: u < v iff d_u < d_v or (d_u = d_v and u < v)
 //   a5  N+ lists (Fig. 1): sort the oriented keys, effective degrees, offsets, columns
 //   tasks: each oriented edge owned by the endpoint with the longer list; tasks whose
-//       partner list is empty are dropped; sorted by (owner, partner); 16-byte records.
+//       partner list is empty are dropped; sorted by (class, owner, position of the oriented
+//       edge in the lists); 16-byte records.
 #include <climits>
 
 #include "graph.cuh"

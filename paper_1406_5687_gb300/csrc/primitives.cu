@@ -134,6 +134,24 @@ __global__ void k_os_bases(unsigned long long* ghist) {
 
 constexpr size_t kOsSmem = (size_t)kOsTile * 8 + (size_t)kOsWarps * kRadix * 4 + 264 * 4 + kRadix * 8;
 
+// Poll *p until it is nonzero; give up (return 0) once `spins`, shared by the caller's
+// successive waits, exceeds `limit`.  Every device wait of the library goes through here.
+__device__ __forceinline__ unsigned long long wait_nonzero(const unsigned long long* p, long long limit,
+                                                           long long& spins) {
+    for (;;) {
+        const unsigned long long v = *(const volatile unsigned long long*)p;
+        if (v != 0) return v;
+        if (++spins > limit) return 0;
+    }
+}
+
+// One thread waits on a flag that nothing sets: the wait must give up after `limit` polls
+// and record TC_ERR_TIMEOUT.
+__global__ void k_wait_selftest(const unsigned long long* flag, long long limit, DevStatus* err) {
+    long long spins = 0;
+    if (wait_nonzero(flag, limit, spins) == 0) set_error(err, TC_ERR_TIMEOUT, spins);
+}
+
 __global__ void __launch_bounds__(kOsBlock, 4) k_os_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                                       int64_t n, int shift, const unsigned long long* __restrict__ base,
                                                       unsigned long long* status, unsigned* tile_counter,
@@ -194,15 +212,12 @@ __global__ void __launch_bounds__(kOsBlock, 4) k_os_pass(const uint64_t* __restr
             long long j = tile - 1;
             long long spins = 0;
             for (;;) {
-                const unsigned long long v = *(volatile unsigned long long*)&status[j * kRadix + d];
-                const unsigned long long f = v & ~kCountMask;
-                if (f == 0) {
-                    if (++spins > spin_limit) {
-                        set_error(err, TC_ERR_TIMEOUT, tile);
-                        break;
-                    }
-                    continue;
+                const unsigned long long v = wait_nonzero(&status[j * kRadix + d], spin_limit, spins);
+                if (v == 0) {
+                    set_error(err, TC_ERR_TIMEOUT, tile);
+                    break;
                 }
+                const unsigned long long f = v & ~kCountMask;
                 excl += v & kCountMask;
                 if (f == kFlagPrefix || j == 0) break;
                 --j;
@@ -287,3 +302,20 @@ tc_status radix_sort_u64(uint64_t* keys, uint64_t* tmp, int64_t n, int lo_bit, i
 }  // namespace tcg
 
 extern "C" int64_t tc_kernel_launches(void) { return (int64_t)tcg::g_launches.load(); }
+
+extern "C" tc_status tc_wait_selftest(int64_t spin_limit, tc_stream_t stream) {
+    using namespace tcg;
+    if (spin_limit < 1) return TC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Allocator al;
+    DevBuf<unsigned long long> buf;  // [0]: the flag (never set), [1..]: the status word
+    TC_TRY(buf.alloc(&al, 1 + (sizeof(DevStatus) + 7) / 8, s));
+    TC_CUDA_TRY(cudaMemsetAsync(buf.ptr, 0, buf.count * 8, s));
+    k_wait_selftest<<<1, 1, 0, s>>>(buf.ptr, (long long)spin_limit, (DevStatus*)(buf.ptr + 1));
+    note_launch();
+    TC_CUDA_TRY(cudaGetLastError());
+    DevStatus h;
+    TC_CUDA_TRY(cudaMemcpyAsync(&h, buf.ptr + 1, sizeof(h), cudaMemcpyDeviceToHost, s));
+    TC_CUDA_TRY(cudaStreamSynchronize(s));
+    return (tc_status)h.code;
+}

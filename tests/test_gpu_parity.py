@@ -330,3 +330,31 @@ def test_er_golden():
         assert g.count() == int(gold["triangles"])
         T, tv = g.count_per_vertex()
         assert int(tv.sum().item()) == int(gold["sum_t_v"])
+
+
+def test_bounded_wait_gives_up_and_the_context_survives():
+    """A device wait on a flag that nothing sets returns TC_ERR_TIMEOUT after its limit."""
+    from paper_1406_5687_gb300 import _lib
+    lib = _lib.load()
+    stream = torch.cuda.current_stream()
+    for limit in (1, 1000, 100_000):
+        assert lib.tc_wait_selftest(limit, tc._stream(stream)) == _lib.TC_ERR_TIMEOUT
+    assert lib.tc_wait_selftest(0, None) == _lib.TC_ERR_INVALID_ARG
+    n, s, d = GRAPHS["cl_200k"]
+    with tc.Graph.build(s, d, n) as g:
+        assert g.count() == oracle.count(oracle_csr(n, s, d))
+
+
+def test_tiny_wait_limits_fail_cleanly_or_count_exactly():
+    """With a look-back / queue limit of a few polls a build or count may give up: it then
+    reports TC_ERR_TIMEOUT instead of a wrong total, and the next call works."""
+    n, s, d = GRAPHS["cl_200k"]
+    want = oracle.count(oracle_csr(n, s, d))
+    for limit in (1, 4):
+        try:
+            with tc.Graph.build(s, d, n, tc.default_options(retry_limit=limit)) as g:
+                assert g.count() == want
+        except tc.TcError as e:
+            assert e.code == tc._lib.TC_ERR_TIMEOUT
+    with tc.Graph.build(s, d, n) as g:
+        assert g.count() == want
