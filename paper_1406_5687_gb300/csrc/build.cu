@@ -363,8 +363,12 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         note_launch();
     }
     TC_CUDA_TRY(cudaGetLastError());
+    // a5: group the oriented edges by owner.  The distinct keys arrive sorted by (min, max),
+    // so a stable sort on the owner bits alone leaves every list ascending: an owner v's
+    // partners below v come from earlier runs (keys (u, v), u ascending), its partners above v
+    // from v's own run (keys (v, x), x ascending), in that order.
     uint64_t* osorted = nullptr;
-    TC_TRY(radix_sort_u64(spare, ukeys, mh, 0, nbits, al, s, &osorted, g->status, spin));
+    TC_TRY(radix_sort_u64(spare, ukeys, mh, b, b, al, s, &osorted, g->status, spin));
     TC_TRY(check_device_error(g, s));
     uint64_t* free_buf = osorted == spare ? ukeys : spare;
     // a5

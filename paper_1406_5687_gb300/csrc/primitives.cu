@@ -1,9 +1,5 @@
-// primitives.cu -- LSD radix sort (step a2's sort) and the single-block scan.
-//
-// Each 8-bit pass is reduce-then-scan: a per-tile digit histogram, one device-wide
-// exclusive scan of the digit-major counts, and a scatter that ranks the tile's keys
-// stably in shared memory (warp match + per-warp digit counters) and writes every digit
-// run contiguously.  No block waits on another block.
+// primitives.cu -- LSD radix sort (the sorts of steps a2 and a5 and of the task array), the
+// single-block scan, the library's bounded device wait and its launch counter.
 #include <atomic>
 #include <mutex>
 
@@ -84,10 +80,22 @@ __global__ void k_scan_single_block(uint64_t* v, int64_t n) {
 // A tile waits only on tiles taken earlier, whose blocks are already running; every wait
 // is bounded and sets the error word when it gives up.
 
-constexpr int kOsBlock = 256;
+// Tile shape: threads per block, keys per thread, and the blocks per SM the register
+// budget is sized for (the block must have at least 256 threads: one per digit).
+#ifndef TC_OS_BLOCK
+#define TC_OS_BLOCK 256
+#endif
+#ifndef TC_OS_ITEMS
+#define TC_OS_ITEMS 16
+#endif
+#ifndef TC_OS_MINB
+#define TC_OS_MINB 4
+#endif
+constexpr int kOsBlock = TC_OS_BLOCK;
 constexpr int kOsWarps = kOsBlock / 32;
-constexpr int kOsItems = 16;
-constexpr int kOsTile = kOsBlock * kOsItems;  // 4096 keys
+constexpr int kOsItems = TC_OS_ITEMS;
+constexpr int kOsTile = kOsBlock * kOsItems;
+static_assert(kOsBlock >= 256 && kOsBlock % 32 == 0, "one thread per digit");
 constexpr int kRadix = 256;
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPrefix = 2ull << 62;
@@ -152,7 +160,7 @@ __global__ void k_wait_selftest(const unsigned long long* flag, long long limit,
     if (wait_nonzero(flag, limit, spins) == 0) set_error(err, TC_ERR_TIMEOUT, spins);
 }
 
-__global__ void __launch_bounds__(kOsBlock, 4) k_os_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+__global__ void __launch_bounds__(kOsBlock, TC_OS_MINB) k_os_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                                       int64_t n, int shift, const unsigned long long* __restrict__ base,
                                                       unsigned long long* status, unsigned* tile_counter,
                                                       DevStatus* err, long long spin_limit) {
