@@ -133,6 +133,8 @@ typedef struct tc_graph* tc_graph_t;
  * Sec. III-A, the N+ lists of Fig. 1 (sorted ascending), and the owner-grouped
  * task array.
  *   src, dst  host or device, m int32 each: edge i is (src[i], dst[i]); never modified.
+ *             Pinned (page-locked) host lists are read in place by the first kernel;
+ *             pageable ones are copied to device memory first.
  *   m         number of input pairs (>= 0).
  *   n         number of vertices, 0 <= n <= 2^30 (TC_ERR_UNSUPPORTED beyond);
  *             at most 2^32 - 2 distinct edges.

@@ -37,6 +37,18 @@ tc_status check_options(const tc_options& o) {
     return TC_OK;
 }
 
+// The device address of pinned (page-locked, mapped) host memory, or null for any other
+// memory.  Kernels read such memory directly over the host link.
+static const void* pinned_device_view(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 static bool is_device_pointer(const void* p) {
     if (!p) return false;
     cudaPointerAttributes at;
@@ -191,7 +203,14 @@ tc_status tc_build(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
         const int32_t* s_d = src;
         const int32_t* d_d = dst;
         DevBuf<int32_t> ss, dd;
-        if (m > 0 && !dev_in) {
+        // pinned host lists are read in place by the canonicalize kernel (one pass over the
+        // host link, no staging copy); pageable ones are staged in device memory first
+        const int32_t* s_pin = m > 0 && !dev_in ? (const int32_t*)pinned_device_view(src) : nullptr;
+        const int32_t* d_pin = m > 0 && !dev_in ? (const int32_t*)pinned_device_view(dst) : nullptr;
+        if (s_pin && d_pin) {
+            s_d = s_pin;
+            d_d = d_pin;
+        } else if (m > 0 && !dev_in) {
             st = ss.alloc(&g->al, (size_t)m, s);
             if (st == TC_OK) st = dd.alloc(&g->al, (size_t)m, s);
             if (st == TC_OK && (cudaMemcpyAsync(ss.ptr, src, (size_t)m * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||

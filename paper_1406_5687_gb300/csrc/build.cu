@@ -143,9 +143,15 @@ __global__ void k_degree(const uint64_t* __restrict__ ukeys, int64_t mh, int b, 
         bool in = i < mh;
         uint64_t k = in ? ukeys[i] : 0;
         uint32_t a = in ? (uint32_t)(k >> b) : 0xFFFFFFFFu;
-        // keys are sorted by their smaller endpoint: aggregate equal ones within the warp
-        unsigned peers = __match_any_sync(kFull, a);
-        if (in && lane == __ffs(peers) - 1) atomicAdd(&deg[a], __popc(peers));
+        // keys are sorted by their smaller endpoint, so equal ones form runs of lanes: the
+        // first lane of each run adds the run's length
+        const uint32_t prev = __shfl_up_sync(kFull, a, 1);
+        const bool head = in && (lane == 0 || a != prev);
+        const unsigned heads = __ballot_sync(kFull, head);
+        const int n_in = __popc(__ballot_sync(kFull, in));  // valid lanes are 0 .. n_in - 1
+        const unsigned after = heads & ~lanemask_le();
+        const int run_end = after ? __ffs(after) - 1 : n_in;
+        if (head) atomicAdd(&deg[a], run_end - lane);
         if (in) atomicAdd(&deg[(uint32_t)(k & mask)], 1);
     }
 }

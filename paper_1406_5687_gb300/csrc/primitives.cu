@@ -189,7 +189,15 @@ __global__ void __launch_bounds__(kOsBlock, TC_OS_MINB) k_os_pass(const uint64_t
         const bool valid = i < n;
         key[j] = valid ? in[i] : 0;
         const unsigned d = valid ? (unsigned)((key[j] >> shift) & 0xFF) : 256u;
-        const unsigned peers = __match_any_sync(kFull, d);
+        // lanes holding the same digit: one ballot per digit bit (cheaper than a warp match);
+        // lanes past the end form a group of their own
+        const unsigned vmask = __ballot_sync(kFull, valid);
+        unsigned peers = valid ? vmask : ~vmask;
+#pragma unroll
+        for (int bt = 0; bt < 8; ++bt) {
+            const unsigned bit = (d >> bt) & 1u;
+            peers &= __ballot_sync(kFull, bit) ^ (bit - 1u);
+        }
         const int leader = __ffs(peers) - 1;
         uint32_t b = 0;
         if (lane == leader && d < 256u) {
