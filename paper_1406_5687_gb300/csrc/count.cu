@@ -35,7 +35,7 @@ namespace tcg {
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kHashMul = 0x9E3779B1u;  // Knuth's multiplicative constant, 2^32 / golden ratio
-constexpr int kUnroll = 4;                   // list windows of 32 entries loaded before probing
+constexpr int kUnits = 4;  // 16-byte units of partner lists a lane loads per step of warp_batch_count
 
 struct CountArgs {
     const int64_t* off;
@@ -228,142 +228,71 @@ __device__ __forceinline__ HashView region_view(uint32_t* tbl, uint32_t reg) {
 
 // One warp counts a batch of nb <= 32 tasks (lane i holds task i's record and, in
 // `reg`, the table region of that task's owner) against the staged owner lists.
+//
+// The partner lists are read as one stream of 16-byte units: list j covers the aligned
+// units from cols[pstart_j & ~3] to its end, and the lists' units are numbered one after
+// another.  Each step a lane takes four units, 32 apart; the list of its unit is the last
+// list that starts at or before it, found from a bit mask of the lists starting in the
+// 32-unit window (one OR-reduction) and a population count.  Entries of a unit outside its
+// list (before pstart, after the end) are masked.
 template <bool EXTRA>
 __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskRec& r, int nb, uint32_t* __restrict__ tbl,
                                                  uint32_t reg, int lane, uint32_t& cnt) {
     const uint32_t len = lane < nb ? r.plen : 0u;
-    // Partner lists of 32 or more entries are cut into chunks of 128 entries aligned to 16
-    // bytes; the warp takes four chunks per step (possibly of different lists), each lane
-    // loading one int4 of each.  A chunk is warp-uniform, so its list is found with one
-    // ballot over the lanes' chunk prefix.
-    {
-        const bool lng = len >= 32u;
-        const uint32_t s0 = r.pstart & ~3u;                               // 16-byte aligned start
-        const uint32_t nch = lng ? (((r.pstart & 3u) + len + 127u) >> 7) : 0u;  // chunks of this list
-        const uint32_t cincl = warp_inclusive_scan(nch, lane);
-        const uint32_t cexcl = cincl - nch;
-        const uint32_t ctot = __shfl_sync(kFull, cincl, 31);
-        for (uint32_t c0 = 0; c0 < ctot; c0 += 4) {
-            int4 v[4];
-            uint32_t lo[4], hi[4], e0[4], rg[4];
-            uint32_t ow[4], pa[4];
+    const uint32_t units = len != 0u ? (((r.pstart & 3u) + len + 3u) >> 2) : 0u;
+    const uint32_t uincl = warp_inclusive_scan(units, lane);
+    const uint32_t ustart = uincl - units;
+    const uint32_t U = __shfl_sync(kFull, uincl, 31);
+    uint32_t before = 0;  // lists that start before the current window
+    for (uint32_t w0 = 0; w0 < U; w0 += 32u * kUnits) {
+        int4 v[kUnits];
+        uint32_t lo[kUnits], ln[kUnits], e0[kUnits], rg[kUnits];
+        uint32_t ow[kUnits], pa[kUnits];
+        bool in[kUnits];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint32_t c = c0 + u;
-                const unsigned who = __ballot_sync(kFull, nch != 0u && cexcl <= c);
-                const int j = 31 - __clz(who);  // list holding chunk c (any lane when c >= ctot)
-                const uint32_t it = c - __shfl_sync(kFull, cexcl, j);
-                lo[u] = __shfl_sync(kFull, r.pstart, j);
-                hi[u] = lo[u] + __shfl_sync(kFull, len, j);
-                rg[u] = __shfl_sync(kFull, reg, j);
-                if (EXTRA) {
-                    ow[u] = __shfl_sync(kFull, r.owner, j);
-                    pa[u] = __shfl_sync(kFull, r.partner, j);
-                }
-                e0[u] = __shfl_sync(kFull, s0, j) + it * 128u + 4u * (uint32_t)lane;
-                if (c < ctot && e0[u] < hi[u]) v[u] = __ldg(reinterpret_cast<const int4*>(a.cols + e0[u]));
-                else v[u] = make_int4(-1, -1, -1, -1);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (c0 + u >= ctot) break;
-                const HashView hv = region_view(tbl, rg[u]);
-                const uint32_t xs[4] = {(uint32_t)v[u].x, (uint32_t)v[u].y, (uint32_t)v[u].z, (uint32_t)v[u].w};
-                bool ok[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) ok[k] = e0[u] + (uint32_t)k - lo[u] < hi[u] - lo[u];
-                if (!EXTRA) {
-                    uint32_t more;
-                    cnt += probe_batch<4>(hv, xs, ok, more);
-                    while (more) {
-                        const int k = __ffs(more) - 1;
-                        more &= more - 1;
-                        cnt += hash_probe_rest(hv, xs[k], (hash_start(hv, xs[k]) + 2) & hv.cmask) ? 1u : 0u;
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const bool hit = ok[k] && hash_probe(hv, xs[k]);
-                        cnt += hit ? 1u : 0u;
-                        if (hit) on_hit<EXTRA>(a, ow[u], pa[u], xs[k]);
-                    }
-                }
-            }
-        }
-    }
-    // shorter lists: gather them into lanes 0..ns-1, then concatenate their entries and
-    // spread them over the lanes
-    const uint32_t short_len = len < 32u ? len : 0u;
-    const unsigned smask = __ballot_sync(kFull, short_len != 0u);
-    if (smask == 0u) return;
-    const int ns = __popc(smask);
-    const int src = lane < ns ? nth_set_bit(smask, lane) : 0;
-    const uint32_t g_len = __shfl_sync(kFull, short_len, src);
-    const uint32_t g_start = __shfl_sync(kFull, r.pstart, src);
-    const uint32_t g_reg = __shfl_sync(kFull, reg, src);
-    uint32_t g_partner = 0, g_owner = 0;
-    if (EXTRA) {
-        g_partner = __shfl_sync(kFull, r.partner, src);
-        g_owner = __shfl_sync(kFull, r.owner, src);
-    }
-    const uint32_t slen = lane < ns ? g_len : 0u;
-    const uint32_t incl = warp_inclusive_scan(slen, lane);
-    const uint32_t excl = incl - slen;
-    const uint32_t tot = __shfl_sync(kFull, incl, 31);
-    uint32_t before = 0;  // gathered tasks whose entries start before the current window
-    for (uint32_t base = 0; base < tot; base += 32u * kUnroll) {
-        uint32_t wv[kUnroll], rg[kUnroll];
-        bool ok[kUnroll];
-        int qj[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const uint32_t wb = base + 32u * u;
-            const uint32_t rel = excl - wb;
-            const uint32_t bit = (slen != 0u && rel < 32u) ? (1u << rel) : 0u;
+        for (int u = 0; u < kUnits; ++u) {
+            const uint32_t wb = w0 + 32u * (uint32_t)u;
+            const uint32_t rel = ustart - wb;
+            const uint32_t bit = (units != 0u && rel < 32u) ? (1u << rel) : 0u;
             const uint32_t starts = __reduce_or_sync(kFull, bit);
-            // entry g = wb + lane belongs to the last gathered task whose first entry is at or
-            // before g; gathered task k sits in lane k
             const int q = ((int)(before + __popc(starts & lanemask_le())) - 1) & 31;
-            const uint32_t sj = __shfl_sync(kFull, g_start, q);
-            const uint32_t ej = __shfl_sync(kFull, excl, q);
-            rg[u] = __shfl_sync(kFull, g_reg, q);
-            const uint32_t g = wb + lane;
-            ok[u] = g < tot;
-            wv[u] = ok[u] ? (uint32_t)__ldg(&a.cols[(long long)sj + (g - ej)]) : 0u;
-            qj[u] = q;
             before += __popc(starts);
+            lo[u] = __shfl_sync(kFull, r.pstart, q);
+            ln[u] = __shfl_sync(kFull, len, q);
+            rg[u] = __shfl_sync(kFull, reg, q);
+            const uint32_t us = __shfl_sync(kFull, ustart, q);
+            if (EXTRA) {
+                ow[u] = __shfl_sync(kFull, r.owner, q);
+                pa[u] = __shfl_sync(kFull, r.partner, q);
+            }
+            const uint32_t unit = wb + (uint32_t)lane;
+            in[u] = unit < U;
+            e0[u] = (lo[u] & ~3u) + 4u * (unit - us);
+            v[u] = in[u] ? __ldg(reinterpret_cast<const int4*>(a.cols + e0[u])) : make_int4(-1, -1, -1, -1);
         }
-        if (!EXTRA) {
-            // entries of different tasks may sit in different owner regions: look up each
-            // entry's first bucket, then finish the rare unresolved ones
-            uint32_t h[kUnroll];
-            uint2 b[kUnroll];
-            const uint32_t* base_p[kUnroll];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const HashView hv = region_view(tbl, rg[u]);
-                base_p[u] = hv.tbl;
-                h[u] = hash_start(hv, wv[u]);
-                b[u] = *reinterpret_cast<const uint2*>(hv.tbl + h[u]);
-            }
+        for (int u = 0; u < kUnits; ++u) {
+            if (w0 + 32u * (uint32_t)u >= U) break;
+            const HashView hv = region_view(tbl, rg[u]);
+            const uint32_t xs[4] = {(uint32_t)v[u].x, (uint32_t)v[u].y, (uint32_t)v[u].z, (uint32_t)v[u].w};
+            bool ok[4];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const bool hit = b[u].x == wv[u] || b[u].y == wv[u];
-                const bool end = b[u].x == kEmpty || b[u].y == kEmpty;
-                cnt += (ok[u] && hit) ? 1u : 0u;
-                if (ok[u] && !hit && !end) {
-                    const HashView hv = region_view(tbl, rg[u]);
-                    cnt += hash_probe_rest(hv, wv[u], (h[u] + 2) & hv.cmask) ? 1u : 0u;
+            for (int k = 0; k < 4; ++k) ok[k] = in[u] && e0[u] + (uint32_t)k - lo[u] < ln[u];
+            if (!EXTRA) {
+                uint32_t more;
+                cnt += probe_batch<4>(hv, xs, ok, more);
+                while (more) {
+                    const int k = __ffs(more) - 1;
+                    more &= more - 1;
+                    cnt += hash_probe_rest(hv, xs[k], (hash_start(hv, xs[k]) + 2) & hv.cmask) ? 1u : 0u;
                 }
-            }
-        } else {
+            } else {
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const bool hit = ok[u] && hash_probe(region_view(tbl, rg[u]), wv[u]);
-                cnt += hit ? 1u : 0u;
-                const uint32_t pj = __shfl_sync(kFull, g_partner, qj[u]);
-                const uint32_t oj = __shfl_sync(kFull, g_owner, qj[u]);
-                if (hit) on_hit<EXTRA>(a, oj, pj, wv[u]);
+                for (int k = 0; k < 4; ++k) {
+                    const bool hit = ok[k] && hash_probe(hv, xs[k]);
+                    cnt += hit ? 1u : 0u;
+                    if (hit) on_hit<EXTRA>(a, ow[u], pa[u], xs[k]);
+                }
             }
         }
     }
