@@ -162,33 +162,39 @@ def stored_traffic(workload):
     return rec.get("dram_bytes_per_launch")
 
 
-def algorithmic_bytes(g, piece, small_max):
-    """Bytes the count kernels must move per count if nothing were cached, for each class and
-    in total: every task reads its 16-byte record and streams its partner list once per piece
-    of its owner's list (4 B per entry); every owner stages its own list once (4 B per entry)
-    and reads its two offsets (16 B).  Also returns the merge-model figure
-    4 (sum_{(v,u)} |N+(u)| + m_hat) + 16 n of the paper's direction of Fig. 1."""
+def algorithmic_bytes(g, opt):
+    """Bytes the count kernels must move per count if nothing were cached, per class.
+
+    Every task reads its 16-byte record and the partner-list entries its kernel must test:
+    a small owner's partner list whole; for a big owner, only the part inside the owner
+    list's [first, last] range (both lists are ascending), found with the list's first and
+    last entry (8 bytes) and a binary search.  Every owner's list is staged once (4 B per
+    entry) with its two offsets (16 B), a big owner also reading its first and last entry
+    (8 B).  The entries read are counted by the kernels themselves in one traced count
+    (`streamed`).  Also returns the merge-direction figure 4 (sum_{(v,u)} |N+(u)| + m_hat)
+    + 16 n of the paper's Fig. 1."""
     import numpy as np
+    _, meta, _, _ = g.count_ex(opt, streamed=True)
+    streamed = meta["streamed"]
     deg, off, cols, tasks = g.csr()
     off = off.cpu().numpy()
-    t = tasks.cpu().numpy()
+    owner = tasks[:, 0].cpu().numpy()
     dh = np.diff(off)
     info = g.info()
     ts = int(info["tasks_small"])
-    owner = t[:, 0].astype(np.int64)
-    plen = t[:, 3].astype(np.int64)
-    pieces = np.where(dh[owner] <= small_max, 1, (dh[owner] + piece - 1) // piece)
 
-    def part(lo, hi):
-        o = owner[lo:hi]
-        streamed = int((pieces[lo:hi] * plen[lo:hi]).sum())
-        owners = np.unique(o)
-        return {"bytes": streamed * 4 + int(dh[owners].sum()) * 4 + 16 * (hi - lo) + 16 * len(owners),
-                "streamed_entries": streamed, "owners": int(len(owners)), "tasks": int(hi - lo)}
+    def part(lo, hi, cls):
+        owners = np.unique(owner[lo:hi])
+        nt = hi - lo
+        b = 16 * nt + 4 * streamed[cls] + 4 * int(dh[owners].sum()) + 16 * len(owners)
+        if cls == 1:
+            b += 8 * nt + 8 * len(owners)
+        return {"bytes": int(b), "streamed_entries": int(streamed[cls]), "owners": int(len(owners)), "tasks": int(nt)}
 
-    small, big = part(0, ts), part(ts, len(t))
+    small, big = part(0, ts, 0), part(ts, len(owner), 1)
     b_merge = 4 * (int(info["sum_dhat_u"]) + int(info["m_hat"])) + 16 * int(info["n"])
-    return {"small": small, "big": big, "total": small["bytes"] + big["bytes"], "merge": b_merge}
+    return {"small": small, "big": big, "total": small["bytes"] + big["bytes"], "merge": b_merge,
+            "untrimmed_big_entries": int(info["sum_stream"]) - int(streamed[0])}
 
 
 def cpu_baseline(workload, pairs, threads=1):
@@ -649,7 +655,7 @@ def run_gpu(args, rank, world, local):
     g = tc.Graph.build(s_dev, d_dev, spec.n, opt)
     info = g.info()
     T_ref = g.count()
-    alg = algorithmic_bytes(g, opt.piece, opt.small_max)
+    alg = algorithmic_bytes(g, opt)
     g.free()
     m_hat = info["m_hat"]
 

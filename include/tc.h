@@ -250,7 +250,10 @@ tc_status tc_vertex_cost(tc_graph_t g, int32_t fn, tc_stream_t stream, uint64_t*
  *            and on return: n_chunks (records produced), and per class c:
  *            n_workers[c] (W), total_cost[c] (C), min_chunk[c] (the Eq. 2 floor
  *            used); tasks_small; the CUDA-event times of the cost prefix and
- *            schedule set-up (prefix_ms) and of each class's kernel.
+ *            schedule set-up (prefix_ms) and of each class's kernel; with
+ *            count_streamed set, streamed[c]: the partner-list entries class c's kernel
+ *            read (big owners read only the part of each partner list inside the owner
+ *            list's [first, last] range).  Counting adds one atomic per warp batch.
  * With trace != NULL the call synchronises `stream` before returning.
  */
 typedef struct tc_count_trace {
@@ -265,7 +268,8 @@ typedef struct tc_count_trace {
     float prefix_ms;        /* a6: task costs, prefix, schedule set-up */
     float kernel_small_ms;  /* a7-a8, small-owner kernel */
     float kernel_big_ms;    /* a7-a8, big-owner kernel */
-    float reserved;
+    int32_t count_streamed; /* in: nonzero = count the partner-list entries each kernel reads */
+    int64_t streamed[2];    /* out: those entries per class (after trimming), or -1 */
 } tc_count_trace;
 
 tc_status tc_count_ex(tc_graph_t g, const tc_options* opt, tc_stream_t stream, uint64_t* total,

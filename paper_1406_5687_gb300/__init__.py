@@ -172,7 +172,7 @@ class Graph:
         return cc[:n]
 
     def count_ex(self, options: _lib.Options | None = None, trace_cap: int = 0, busy: bool = False, stream=None,
-                 timing: bool = False):
+                 timing: bool = False, streamed: bool = False):
         """Count with explicit options; optionally record the schedule.
 
         Returns (T, meta, chunks, busy): chunks is an int64 CUDA tensor of shape (k, 5)
@@ -191,15 +191,16 @@ class Graph:
             # small-class warps (at most 64 resident per SM) plus big-class blocks (at most 32 per SM)
             bz = torch.zeros(2 * sms * 96, dtype=torch.int64, device="cuda")
             tr.workers_busy = bz.data_ptr()
+        tr.count_streamed = 1 if streamed else 0
         t = ctypes.c_uint64()
         opt = ctypes.byref(options) if options is not None else None
-        use_trace = trace_cap > 0 or busy or timing
+        use_trace = trace_cap > 0 or busy or timing or streamed
         _lib.check(load().tc_count_ex(self._h, opt, _stream(stream), ctypes.byref(t),
                                       ctypes.byref(tr) if use_trace else None), "tc_count_ex")
         meta = {"n_chunks": tr.n_chunks, "n_workers": list(tr.n_workers), "total_cost": list(tr.total_cost),
                 "min_chunk": list(tr.min_chunk), "tasks_small": tr.tasks_small, "prefix_ms": tr.prefix_ms,
                 "kernel_small_ms": tr.kernel_small_ms, "kernel_big_ms": tr.kernel_big_ms,
-                "kernel_ms": tr.kernel_small_ms + tr.kernel_big_ms}
+                "kernel_ms": tr.kernel_small_ms + tr.kernel_big_ms, "streamed": list(tr.streamed)}
         chunks = None
         if ch is not None:
             raw = ch.view(-1, 4)[:min(tr.n_chunks, trace_cap)]

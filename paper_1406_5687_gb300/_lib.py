@@ -61,7 +61,8 @@ class CountTrace(ctypes.Structure):
     _fields_ = [("chunks", ctypes.c_void_p), ("cap", ctypes.c_int64), ("workers_busy", ctypes.c_void_p),
                 ("n_chunks", ctypes.c_int64), ("n_workers", ctypes.c_int64 * 2), ("total_cost", ctypes.c_uint64 * 2),
                 ("min_chunk", ctypes.c_uint64 * 2), ("tasks_small", ctypes.c_int64), ("prefix_ms", ctypes.c_float),
-                ("kernel_small_ms", ctypes.c_float), ("kernel_big_ms", ctypes.c_float), ("reserved", ctypes.c_float)]
+                ("kernel_small_ms", ctypes.c_float), ("kernel_big_ms", ctypes.c_float),
+                ("count_streamed", ctypes.c_int32), ("streamed", ctypes.c_int64 * 2)]
 
 
 class BatchInfo(ctypes.Structure):

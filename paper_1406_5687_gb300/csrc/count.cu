@@ -63,6 +63,7 @@ struct CountArgs {
     const uint32_t* own_first;  // big class: first task of each owner, then T
     long long n_owners;         // big class: owners
     const int64_t* gtask;       // packs: this class's first task of each graph, then its end
+    unsigned long long* streamed;  // traced counts only: partner entries read, summed per class
     long long n_sub;            // packs: graphs (0: one graph, one total)
 };
 
@@ -226,8 +227,52 @@ __device__ __forceinline__ HashView region_view(uint32_t* tbl, uint32_t reg) {
     return hv;
 }
 
+// Both lists are ascending, so only the partner entries within [omin, omax] (the owner
+// list's first and last entry) can be in the owner's list: shrink the partner list
+// cols[ps, ps + len) to that sub-list.  The two bounds are found by binary searches run
+// side by side; lists already inside the range (the usual case) cost two loads.
+__device__ __forceinline__ void trim_to_range(const int32_t* __restrict__ cols, uint32_t& ps, uint32_t& len,
+                                              uint32_t omin, uint32_t omax) {
+    if (len == 0u) return;
+    const uint32_t first = (uint32_t)__ldg(&cols[ps]), last = (uint32_t)__ldg(&cols[ps + len - 1u]);
+    if (first >= omin && last <= omax) return;
+    if (last < omin || first > omax) {
+        len = 0u;
+        return;
+    }
+    // lb: first entry >= omin; ub: first entry > omax
+    uint32_t lb = ps, nl = first < omin ? len : 0u;
+    uint32_t ub = ps + len, nu = last > omax ? len : 0u;
+    if (nu) ub = ps;
+    while (nl | nu) {
+        if (nl) {
+            const uint32_t h = nl >> 1;
+            if ((uint32_t)__ldg(&cols[lb + h]) < omin) {
+                lb += h + 1u;
+                nl -= h + 1u;
+            } else {
+                nl = h;
+            }
+        }
+        if (nu) {
+            const uint32_t h = nu >> 1;
+            if ((uint32_t)__ldg(&cols[ub + h]) <= omax) {
+                ub += h + 1u;
+                nu -= h + 1u;
+            } else {
+                nu = h;
+            }
+        }
+    }
+    ps = lb;
+    len = ub > lb ? ub - lb : 0u;
+}
+
 // One warp counts a batch of nb <= 32 tasks (lane i holds task i's record and, in
-// `reg`, the table region of that task's owner) against the staged owner lists.
+// `reg`, the table region of that task's owner) against the staged owner lists.  With
+// TRIM (big owners), each partner list is first trimmed to its owner's range [omin, omax];
+// lists left empty drop out and the others are gathered into the low lanes.  Lists of
+// small owners are short and seldom trimmed, so they are read whole.
 //
 // The partner lists are read as one stream of 16-byte units: list j covers the aligned
 // units from cols[pstart_j & ~3] to its end, and the lists' units are numbered one after
@@ -235,11 +280,33 @@ __device__ __forceinline__ HashView region_view(uint32_t* tbl, uint32_t reg) {
 // list that starts at or before it, found from a bit mask of the lists starting in the
 // 32-unit window (one OR-reduction) and a population count.  Entries of a unit outside its
 // list (before pstart, after the end) are masked.
-template <bool EXTRA>
-__device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskRec& r, int nb, uint32_t* __restrict__ tbl,
-                                                 uint32_t reg, int lane, uint32_t& cnt) {
-    const uint32_t len = lane < nb ? r.plen : 0u;
-    const uint32_t units = len != 0u ? (((r.pstart & 3u) + len + 3u) >> 2) : 0u;
+template <bool EXTRA, bool TRIM>
+__device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskRec& rin, int nb, uint32_t* __restrict__ tbl,
+                                                 uint32_t reg_in, uint32_t omin, uint32_t omax, int lane, uint32_t& cnt) {
+    uint32_t ps = rin.pstart, len = lane < nb ? rin.plen : 0u;
+    if (TRIM) trim_to_range(a.cols, ps, len, omin, omax);
+    // the k-th nonempty list in lane k (untrimmed lists are never empty)
+    const unsigned act = __ballot_sync(kFull, len != 0u);
+    const int na = __popc(act);
+    TaskRec r = rin;
+    uint32_t reg = reg_in;
+    if (TRIM && act != (na == 32 ? kFull : (1u << na) - 1u)) {
+        const int src = lane < na ? nth_set_bit(act, lane) : 0;
+        const uint32_t gl = __shfl_sync(kFull, len, src);
+        ps = __shfl_sync(kFull, ps, src);
+        reg = __shfl_sync(kFull, reg_in, src);
+        if (EXTRA) {
+            r.owner = __shfl_sync(kFull, rin.owner, src);
+            r.partner = __shfl_sync(kFull, rin.partner, src);
+        }
+        len = lane < na ? gl : 0u;
+    }
+    r.pstart = ps;
+    if (a.streamed) {
+        const uint32_t tot = warp_sum(len);
+        if (lane == 0 && tot) atomicAdd(a.streamed, (unsigned long long)tot);
+    }
+    const uint32_t units = len != 0u ? (((ps & 3u) + len + 3u) >> 2) : 0u;
     const uint32_t uincl = warp_inclusive_scan(units, lane);
     const uint32_t ustart = uincl - units;
     const uint32_t U = __shfl_sync(kFull, uincl, 31);
@@ -298,11 +365,11 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
     }
 }
 
-template <bool EXTRA>
+template <bool EXTRA, bool TRIM>
 __device__ void warp_batch(const CountArgs& a, const TaskRec& r, int nb, uint32_t* __restrict__ tbl, uint32_t reg,
-                           int lane, unsigned long long& acc) {
+                           uint32_t omin, uint32_t omax, int lane, unsigned long long& acc) {
     uint32_t cnt = 0;  // this lane's hits in the batch (fits 32 bits: at most 32 lists of < 2^17 entries)
-    warp_batch_count<EXTRA>(a, r, nb, tbl, reg, lane, cnt);
+    warp_batch_count<EXTRA, TRIM>(a, r, nb, tbl, reg, omin, omax, lane, cnt);
     acc += cnt;
 }
 
@@ -402,7 +469,7 @@ __device__ void process_small(const CountArgs& a, long long t0, long long t1, ui
             before += __popc(starts);
         }
         __syncwarp();
-        warp_batch<EXTRA>(a, r, nt, tbl, reg, lane, acc);
+        warp_batch<EXTRA, false>(a, r, nt, tbl, reg, 0u, 0xFFFFFFFFu, lane, acc);
         __syncwarp();
         t += nt;
     }
@@ -436,6 +503,8 @@ struct BigWindow {
     long long ob[kWinOwners];         // owner i's list: cols[ob[i], ob[i] + ol[i])
     uint32_t ol[kWinOwners];
     uint32_t reg[kWinOwners];         // owner i's table region
+    uint32_t lmin[kWinOwners];        // owner i's first and last list entry
+    uint32_t lmax[kWinOwners];
     long long k;                      // owner index of the window's first owner
     uint32_t used;                    // table slots in use
     int nown;                         // owners in the window; 0: one owner needs several pieces
@@ -456,6 +525,7 @@ __device__ void big_owner_pieces(const CountArgs& a, long long t, long long tend
         if (threadIdx.x == 0) *s_next = 0;
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < pl; i += blockDim.x) hash_insert(hv, (uint32_t)__ldg(&a.cols[ob + ps + i]));
+        const uint32_t pmin = (uint32_t)__ldg(&a.cols[ob + ps]), pmax = (uint32_t)__ldg(&a.cols[ob + ps + pl - 1]);
         __syncthreads();
         for (;;) {
             unsigned b = 0;
@@ -466,7 +536,7 @@ __device__ void big_owner_pieces(const CountArgs& a, long long t, long long tend
             const int nb = (int)(tend - tb < 32 ? tend - tb : 32);
             TaskRec r = {0u, 0u, 0u, 0u};
             if (lane < nb) r = a.tasks[tb + lane];
-            warp_batch<EXTRA>(a, r, nb, tbl, reg, lane, acc);
+            warp_batch<EXTRA, true>(a, r, nb, tbl, reg, pmin, pmax, lane, acc);
         }
         __syncthreads();
     }
@@ -496,7 +566,7 @@ __device__ void process_big(const CountArgs& a, long long t0, long long t1, uint
             const long long kq = k + lane;
             const bool exists = kq < a.n_owners && (long long)a.own_first[kq] < t1;
             long long ob = 0, first = 0;
-            uint32_t ol = 0, cap = 0;
+            uint32_t ol = 0, cap = 0, lmin = 0u, lmax = 0u;
             if (exists) {
                 first = (long long)a.own_first[kq];
                 const uint32_t owner = a.tasks[first].owner;
@@ -504,6 +574,10 @@ __device__ void process_big(const CountArgs& a, long long t0, long long t1, uint
                 ol = (uint32_t)(a.off[owner + 1] - ob);
                 cap = 1024;
                 while (cap < 8 * ol) cap <<= 1;
+                if (ol) {
+                    lmin = (uint32_t)__ldg(&a.cols[ob]);
+                    lmax = (uint32_t)__ldg(&a.cols[ob + ol - 1]);
+                }
             }
             const uint32_t cend = warp_inclusive_scan(cap, lane);
             const unsigned fit = __ballot_sync(kFull, exists && cend <= (uint32_t)a.table_slots);
@@ -514,6 +588,8 @@ __device__ void process_big(const CountArgs& a, long long t0, long long t1, uint
                 w->ob[lane] = ob;
                 w->ol[lane] = ol;
                 w->reg[lane] = pack_region(cend - cap, cap);
+                w->lmin[lane] = lmin;
+                w->lmax[lane] = lmax;
             }
             if (lane == 0) {
                 const long long nk = k + (nown > 0 ? nown : 1);
@@ -548,7 +624,7 @@ __device__ void process_big(const CountArgs& a, long long t0, long long t1, uint
                 if (tb >= tend) break;
                 const int nb = (int)(tend - tb < 32 ? tend - tb : 32);
                 TaskRec r = {0u, 0u, 0u, 0u};
-                uint32_t reg = 0u;
+                uint32_t reg = 0u, omin = 0u, omax = 0u;
                 if (lane < nb) {
                     const long long j = tb + lane;
                     r = a.tasks[j];
@@ -558,8 +634,10 @@ __device__ void process_big(const CountArgs& a, long long t0, long long t1, uint
                         if (w->first[mid] <= j) lo = mid; else hi = mid - 1;
                     }
                     reg = w->reg[lo];
+                    omin = w->lmin[lo];
+                    omax = w->lmax[lo];
                 }
-                warp_batch<EXTRA>(a, r, nb, tbl, reg, lane, acc);
+                warp_batch<EXTRA, true>(a, r, nb, tbl, reg, omin, omax, lane, acc);
             }
             __syncthreads();
         }
@@ -747,6 +825,7 @@ __global__ void k_sched_init(Sched* sc, const uint64_t* P, long long Ts, long lo
         sc[c].head = H;
         sc[c].n_chunks = 0;
         sc[c].base = base;
+        sc[c].streamed = 0;
     }
 }
 
@@ -907,8 +986,10 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     a.own_first = g->own_first;
     a.n_owners = g->owners_big;
     a.n_sub = g->n_sub;
+    const bool count_streamed = trace && trace->count_streamed;
     // small class
     a.gtask = g->sub_task;
+    a.streamed = count_streamed ? &w.sched[0].streamed : nullptr;
     a.t_begin = 0;
     a.t_end = Ts;
     a.sched = w.sched;
@@ -927,6 +1008,7 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     if (trace) TC_CUDA_TRY(cudaEventRecord(ev[2], s));
     // big class
     a.gtask = g->sub_task ? g->sub_task + (g->n_sub + 1) : nullptr;
+    a.streamed = count_streamed ? &w.sched[1].streamed : nullptr;
     a.t_begin = Ts;
     a.t_end = T;
     a.sched = w.sched + 1;
@@ -952,6 +1034,7 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
         for (int c = 0; c < 2; ++c) {
             trace->total_cost[c] = hs[c].C;
             trace->min_chunk[c] = hs[c].min_chunk;
+            trace->streamed[c] = count_streamed ? (int64_t)hs[c].streamed : -1;
         }
         trace->tasks_small = Ts;
         float ms = 0.f;
@@ -1053,6 +1136,7 @@ static tc_status count_enqueue_static(tc_graph* g, cudaStream_t s, unsigned long
     a.own_first = g->own_first;
     a.n_owners = g->owners_big;
     a.gtask = nullptr;
+    a.streamed = nullptr;
     a.n_sub = 0;
     a.t_begin = 0;
     a.t_end = Ts;

@@ -24,6 +24,7 @@ struct Sched {
     unsigned long long head;
     unsigned long long n_chunks;
     unsigned long long base;  // exclusive prefix at the class's first task
+    unsigned long long streamed;  // partner-list entries the class's kernel read (traced counts only)
 };
 
 // Device counters written by the build kernels.

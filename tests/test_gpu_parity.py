@@ -358,3 +358,40 @@ def test_tiny_wait_limits_fail_cleanly_or_count_exactly():
             assert e.code == tc._lib.TC_ERR_TIMEOUT
     with tc.Graph.build(s, d, n) as g:
         assert g.count() == want
+
+
+def _streamed_entries(csr, small_max, piece):
+    """Partner entries each class's kernel must read: a small owner's partner list whole;
+    for a big owner, per piece of its list (pieces of `piece` entries), the part of the
+    partner list within the piece's [first, last] entries (both lists are ascending)."""
+    own, par, ns = oracle.tasks(csr, small_max=small_max, with_split=True)
+    off, cols = csr.off, csr.cols.astype(np.int64)
+    dh = np.diff(off)
+    small = int(dh[par[:ns]].sum())
+    o, p = own[ns:].astype(np.int64), par[ns:].astype(np.int64)
+    key = cols + np.repeat(np.arange(len(dh), dtype=np.int64), dh) * (1 << 32)
+    big = 0
+    npieces = (dh[o] + piece - 1) // piece
+    for k in range(int(npieces.max()) if len(o) else 0):
+        m = npieces > k
+        ob = off[o[m]] + k * piece
+        pl = np.minimum(piece, dh[o[m]] - k * piece)
+        lo_v, hi_v = cols[ob], cols[ob + pl - 1]
+        pm = p[m]
+        lo = np.searchsorted(key, pm * (1 << 32) + lo_v, side="left")
+        hi = np.searchsorted(key, pm * (1 << 32) + hi_v, side="right")
+        big += int((hi - lo).sum())
+    return small, big
+
+
+@pytest.mark.parametrize("name,piece", [("cl_200k", 2048), ("cl_dense", 256), ("ba_30k", 1024)])
+def test_streamed_entries_match_the_host_count(name, piece):
+    n, s, d = GRAPHS[name]
+    csr = oracle_csr(n, s, d)
+    want = _streamed_entries(csr, 64, piece)
+    with tc.Graph.build(s, d, n) as g:
+        T, meta, _, _ = g.count_ex(tc.default_options(piece=piece), streamed=True)
+        assert T == oracle.count(csr)
+        assert tuple(meta["streamed"]) == want
+        _, meta2, _, _ = g.count_ex(tc.default_options(piece=piece), timing=True)
+        assert list(meta2["streamed"]) == [-1, -1]
