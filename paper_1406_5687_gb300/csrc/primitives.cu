@@ -73,10 +73,11 @@ __global__ void k_scan_single_block(uint64_t* v, int64_t n) {
 // LSD radix sort with 8-bit digits and one kernel per digit (the "onesweep" arrangement of
 // Adinets and Merrill, 2022).  One upfront pass counts every digit of every key.  Each
 // digit pass then takes tiles of 4096 keys in the order blocks start (an atomic tile
-// counter), ranks the tile's keys stably in shared memory, publishes the tile's digit
-// counts and obtains the count of each digit in all earlier tiles by a decoupled
-// look-back over their published words (flag in the top two bits: aggregate of the tile
-// alone, or inclusive prefix), then writes every digit run of the tile contiguously.
+// counter), counts the tile's digits and publishes them at once, ranks the tile's keys
+// stably in shared memory while the first look-back load is in flight, and obtains the
+// count of each digit in all earlier tiles by a decoupled look-back over their published
+// words (flag in the top two bits: aggregate of the tile alone, or inclusive prefix), then
+// writes every digit run of the tile contiguously.
 // A tile waits only on tiles taken earlier, whose blocks are already running; every wait
 // is bounded and sets the error word when it gives up.
 
@@ -177,17 +178,43 @@ __global__ void __launch_bounds__(kOsBlock, TC_OS_MINB) k_os_pass(const uint64_t
     const long long tile = (long long)s_tile;
     const int64_t tbase = tile * kOsTile;
 
-    // warp-striped load: lane l holds the warp's keys j*32 + l (memory order j-major), ranked
-    // within the warp by digit
+    // warp-striped load: lane l holds the warp's keys j*32 + l (memory order j-major)
     const int64_t wbase = tbase + (int64_t)warp * 32 * kOsItems;
     uint64_t key[kOsItems];
     uint32_t rank[kOsItems];
     uint32_t* mycnt = wcnt + warp * kRadix;
+    __shared__ uint32_t s_hist[kRadix];
+    if (threadIdx.x < kRadix) s_hist[threadIdx.x] = 0;
+#pragma unroll
+    for (int j = 0; j < kOsItems; ++j) {
+        const int64_t i = wbase + j * 32 + lane;
+        key[j] = i < n ? in[i] : 0;
+    }
+    __syncthreads();
+    // early counts: the tile's digit histogram, published before the ranking so that later
+    // tiles find it sooner; the first look-back load is issued before ranking too
+#pragma unroll
+    for (int j = 0; j < kOsItems; ++j) {
+        const int64_t i = wbase + j * 32 + lane;
+        if (i < n) atomicAdd(&s_hist[(unsigned)((key[j] >> shift) & 0xFF)], 1u);
+    }
+    __syncthreads();
+    unsigned long long* st = status + tile * kRadix;
+    uint32_t run = 0;
+    unsigned long long lb_first = 0;
+    if (threadIdx.x < kRadix) {
+        run = s_hist[threadIdx.x];
+        if (tile == 0) {
+            *(volatile unsigned long long*)&st[threadIdx.x] = kFlagPrefix | run;
+        } else {
+            *(volatile unsigned long long*)&st[threadIdx.x] = kFlagAgg | run;
+            lb_first = *(const volatile unsigned long long*)&status[(tile - 1) * kRadix + threadIdx.x];
+        }
+    }
 #pragma unroll
     for (int j = 0; j < kOsItems; ++j) {
         const int64_t i = wbase + j * 32 + lane;
         const bool valid = i < n;
-        key[j] = valid ? in[i] : 0;
         const unsigned d = valid ? (unsigned)((key[j] >> shift) & 0xFF) : 256u;
         // lanes holding the same digit: one ballot per digit bit (cheaper than a warp match);
         // lanes past the end form a group of their own
@@ -210,25 +237,21 @@ __global__ void __launch_bounds__(kOsBlock, TC_OS_MINB) k_os_pass(const uint64_t
     __syncthreads();
     if (threadIdx.x < kRadix) {
         const int d = threadIdx.x;
-        // per digit: exclusive scan over the warps; `run` ends as the tile's count of d
-        uint32_t run = 0;
+        // per digit: exclusive scan over the warps
+        uint32_t r2 = 0;
 #pragma unroll
         for (int w = 0; w < kOsWarps; ++w) {
             const uint32_t t = wcnt[w * kRadix + d];
-            wcnt[w * kRadix + d] = run;
-            run += t;
+            wcnt[w * kRadix + d] = r2;
+            r2 += t;
         }
-        // publish the tile's count and look back for the counts of all earlier tiles
-        unsigned long long* st = status + tile * kRadix;
         unsigned long long excl = 0;
-        if (tile == 0) {
-            *(volatile unsigned long long*)&st[d] = kFlagPrefix | run;
-        } else {
-            *(volatile unsigned long long*)&st[d] = kFlagAgg | run;
+        if (tile != 0) {
             long long j = tile - 1;
             long long spins = 0;
+            unsigned long long v = lb_first;
             for (;;) {
-                const unsigned long long v = wait_nonzero(&status[j * kRadix + d], spin_limit, spins);
+                if (v == 0) v = wait_nonzero(&status[j * kRadix + d], spin_limit, spins);
                 if (v == 0) {
                     set_error(err, TC_ERR_TIMEOUT, tile);
                     break;
@@ -237,6 +260,7 @@ __global__ void __launch_bounds__(kOsBlock, TC_OS_MINB) k_os_pass(const uint64_t
                 excl += v & kCountMask;
                 if (f == kFlagPrefix || j == 0) break;
                 --j;
+                v = *(const volatile unsigned long long*)&status[j * kRadix + d];
             }
             *(volatile unsigned long long*)&st[d] = kFlagPrefix | (excl + run);
         }
