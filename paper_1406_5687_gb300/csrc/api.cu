@@ -39,7 +39,7 @@ tc_status check_options(const tc_options& o) {
 
 // The device address of pinned (page-locked, mapped) host memory, or null for any other
 // memory.  Kernels read such memory directly over the host link.
-static const void* pinned_device_view(const void* p) {
+const void* pinned_device_view(const void* p) {
     if (!p) return nullptr;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -49,7 +49,7 @@ static const void* pinned_device_view(const void* p) {
     return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
-static bool is_device_pointer(const void* p) {
+bool is_device_pointer(const void* p) {
     if (!p) return false;
     cudaPointerAttributes at;
     cudaError_t e = cudaPointerGetAttributes(&at, p);

@@ -13,19 +13,22 @@
 
 namespace tcg {
 
-// Graph j of a pack: its edges are [ebase[j], ebase[j+1]) of the pack's staging arrays and
+// Graph j of a pack: its edges are [ebase[j], ebase[j+1]) of the pack's edge arrays, read
+// from src[j] / dst[j] (device memory, or pinned host memory read over the host link), and
 // its vertices [vbase[j], vbase[j+1]) of the pack's vertex range.
 struct PackMeta {
-    const int64_t* ebase;  // k + 1
-    const int32_t* vbase;  // k + 1
+    const int64_t* ebase;            // k + 1
+    const int32_t* vbase;            // k + 1
+    const int32_t* const* src;       // k
+    const int32_t* const* dst;       // k
     int32_t k;
 };
 
-// Check every id against its own graph's n and move it into the graph's vertex range.  An id
-// outside [0, n_j) records TC_ERR_VERTEX_RANGE with the pack-wide edge index and is left as
-// it is (the build is abandoned).
-__global__ void k_offset_ids(int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t m, PackMeta pm,
-                             DevStatus* status) {
+// Gather every graph's edges into the pack's arrays, checking each id against its own
+// graph's n and moving it into the graph's vertex range.  An id outside [0, n_j) records
+// TC_ERR_VERTEX_RANGE with the pack-wide edge index (the build is abandoned).
+__global__ void k_pack_ids(PackMeta pm, int64_t m, int32_t* __restrict__ out_src, int32_t* __restrict__ out_dst,
+                           DevStatus* status) {
     int g = 0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
         // graphs are in edge order and e only grows: step forward, else search from g
@@ -37,15 +40,16 @@ __global__ void k_offset_ids(int32_t* __restrict__ src, int32_t* __restrict__ ds
             }
             g = lo;
         }
+        const int64_t l = e - pm.ebase[g];
         const int32_t vb = pm.vbase[g];
         const int32_t nj = pm.vbase[g + 1] - vb;
-        const int32_t a = src[e], b = dst[e];
+        const int32_t a = pm.src[g][l], b = pm.dst[g][l];
         if (a < 0 || a >= nj || b < 0 || b >= nj) {
             set_error(status, TC_ERR_VERTEX_RANGE, e);
             continue;
         }
-        src[e] = a + vb;
-        dst[e] = b + vb;
+        out_src[e] = a + vb;
+        out_dst[e] = b + vb;
     }
 }
 
@@ -130,27 +134,43 @@ static tc_status build_pack(const int32_t* const* src, const int32_t* const* dst
         DevBuf<int32_t> ss, dd;
         DevBuf<int64_t> eb;
         DevBuf<int32_t> vb;
+        DevBuf<const int32_t*> sp, dp;
         st = ss.alloc(&g->al, (size_t)(mp > 0 ? mp : 1), s);
         if (st == TC_OK) st = dd.alloc(&g->al, (size_t)(mp > 0 ? mp : 1), s);
         if (st == TC_OK) st = eb.alloc(&g->al, (size_t)k + 1, s);
         if (st == TC_OK) st = vb.alloc(&g->al, (size_t)k + 1, s);
-        if (st == TC_OK) {
-            // every graph's edges into the pack's staging arrays (host or device sources)
-            for (int32_t j = 0; j < k && st == TC_OK; ++j) {
-                const int64_t mj = m[j0 + j];
-                if (mj == 0) continue;
-                if (cudaMemcpyAsync(ss.ptr + ebase[j], src[j0 + j], (size_t)mj * 4, cudaMemcpyDefault, s) != cudaSuccess ||
-                    cudaMemcpyAsync(dd.ptr + ebase[j], dst[j0 + j], (size_t)mj * 4, cudaMemcpyDefault, s) != cudaSuccess)
-                    st = TC_ERR_CUDA;
+        if (st == TC_OK) st = sp.alloc(&g->al, (size_t)k, s);
+        if (st == TC_OK) st = dp.alloc(&g->al, (size_t)k, s);
+        // where the gather kernel reads each graph: device memory and pinned host memory in
+        // place; pageable host memory is first copied into the graph's part of the pack arrays
+        std::vector<const int32_t*> sv(k, nullptr), dv(k, nullptr);
+        for (int32_t j = 0; j < k && st == TC_OK; ++j) {
+            const int64_t mj = m[j0 + j];
+            if (mj == 0) continue;
+            const int32_t* a = src[j0 + j];
+            const int32_t* b = dst[j0 + j];
+            const int32_t* av = is_device_pointer(a) ? a : (const int32_t*)pinned_device_view(a);
+            const int32_t* bv = is_device_pointer(b) ? b : (const int32_t*)pinned_device_view(b);
+            if (!av) {
+                if (cudaMemcpyAsync(ss.ptr + ebase[j], a, (size_t)mj * 4, cudaMemcpyDefault, s) != cudaSuccess) st = TC_ERR_CUDA;
+                av = ss.ptr + ebase[j];
             }
+            if (!bv) {
+                if (cudaMemcpyAsync(dd.ptr + ebase[j], b, (size_t)mj * 4, cudaMemcpyDefault, s) != cudaSuccess) st = TC_ERR_CUDA;
+                bv = dd.ptr + ebase[j];
+            }
+            sv[j] = av;
+            dv[j] = bv;
         }
         if (st == TC_OK && (cudaMemcpyAsync(eb.ptr, ebase.data(), (size_t)(k + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-                            cudaMemcpyAsync(vb.ptr, vbase.data(), (size_t)(k + 1) * 4, cudaMemcpyHostToDevice, s) != cudaSuccess))
+                            cudaMemcpyAsync(vb.ptr, vbase.data(), (size_t)(k + 1) * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                            cudaMemcpyAsync(sp.ptr, sv.data(), (size_t)k * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                            cudaMemcpyAsync(dp.ptr, dv.data(), (size_t)k * 8, cudaMemcpyHostToDevice, s) != cudaSuccess))
             st = TC_ERR_CUDA;
         if (st == TC_OK && mp > 0) {
             const int64_t want = (mp + 255) / 256;
             const unsigned blocks = (unsigned)std::min<int64_t>(want, (int64_t)num_sms() * 8);
-            k_offset_ids<<<blocks, 256, 0, s>>>(ss.ptr, dd.ptr, mp, PackMeta{eb.ptr, vb.ptr, k}, g->status);
+            k_pack_ids<<<blocks, 256, 0, s>>>(PackMeta{eb.ptr, vb.ptr, sp.ptr, dp.ptr, k}, mp, ss.ptr, dd.ptr, g->status);
             note_launch();
             if (cudaGetLastError() != cudaSuccess) st = TC_ERR_CUDA;
             if (st == TC_OK) st = read_status(g, s, nullptr);

@@ -108,6 +108,11 @@ tc_status new_graph(const tc_options& o, cudaStream_t s, tc_graph** out);
 void free_graph(tc_graph* g);
 tc_status read_status(tc_graph* g, cudaStream_t s, unsigned long long* result);
 
+// Memory kinds (api.cu): device (or managed) memory; the device address of pinned host
+// memory (null for anything else).
+bool is_device_pointer(const void* p);
+const void* pinned_device_view(const void* p);
+
 // Device bytes a build of (m, n) holds at its peak, and a built graph keeps (api.cu).
 int64_t build_peak_bytes(int64_t m, int32_t n, bool host_input);
 int64_t graph_resident_bytes(int64_t m_hat, int64_t tasks, int32_t n);
