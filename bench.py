@@ -57,6 +57,7 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain leg")
     p.add_argument("--no-serve", action="store_true", help="skip the serving-vs-plain leg")
+    p.add_argument("--pack-edges", type=int, default=0, help="input edges per batch pack (0: the library default)")
     p.add_argument("--serve-requests", type=int, default=0,
                    help="requests of the serving window (default: 256 as a leg of a single-graph run, 2000 "
                         "with --workload serve)")
@@ -252,7 +253,7 @@ def batch_inputs(count, threads=None):
         return list(ex.map(gen, specs))
 
 
-def batch_leg(count, steps, warmup, tune_sample=64, oracle_sample=4):
+def batch_leg(count, steps, warmup, tune_sample=64, oracle_sample=4, pack_edges=0):
     """Batched counting of `count` graphs against the plain per-graph path on the same GPU.
 
     batched: tc_batch_build + tc_batch_run per step (edge lists resident in HBM, then from
@@ -280,7 +281,7 @@ def batch_leg(count, steps, warmup, tune_sample=64, oracle_sample=4):
     def batched_step(graphs):
         e0, e1, e2 = ev(), ev(), ev()
         e0.record(stream)
-        b = tc.Batch.build(graphs, options=best, stream=stream)
+        b = tc.Batch.build(graphs, options=best, pack_edges=pack_edges, stream=stream)
         e1.record(stream)
         out = torch.empty(count, dtype=torch.int64, device="cuda")
         b.run(out, stream)
@@ -303,7 +304,7 @@ def batch_leg(count, steps, warmup, tune_sample=64, oracle_sample=4):
     b_count = statistics.mean(r[2] for r in res)
 
     # count only, CSR resident: replays of the captured launch
-    b = tc.Batch.build(dev, options=best, stream=stream)
+    b = tc.Batch.build(dev, options=best, pack_edges=pack_edges, stream=stream)
     out = torch.empty(count, dtype=torch.int64, device="cuda")
     for _ in range(warmup):
         b.run(out, stream)
@@ -322,7 +323,7 @@ def batch_leg(count, steps, warmup, tune_sample=64, oracle_sample=4):
     # e2e: edge lists in pinned host memory, the k totals read back to the host
     def batched_host():
         t = time.perf_counter()
-        bb = tc.Batch.build(host, options=best, stream=stream)
+        bb = tc.Batch.build(host, options=best, pack_edges=pack_edges, stream=stream)
         got = bb.count(stream)
         bb.free()
         return (time.perf_counter() - t) * 1e3, got
@@ -572,7 +573,7 @@ def run_batch_only(args, rank, world, local):
         "CUDA_VISIBLE_DEVICES") else str(local)
     clocks = ClockSampler(gpu_index)
     clocks.start()
-    leg = batch_leg(count, args.steps, args.warmup)
+    leg = batch_leg(count, args.steps, args.warmup, pack_edges=args.pack_edges)
     clk = clocks.stop()
     ms = leg["batched"]["ms"]
     if pg:
@@ -750,7 +751,8 @@ def run_gpu(args, rank, world, local):
 
     batch = None
     if rank == 0 and not args.no_batch:
-        batch = batch_leg(args.batch_graphs or 512, max(2, min(args.steps, 3)), args.warmup)
+        batch = batch_leg(args.batch_graphs or 512, max(2, min(args.steps, 3)), args.warmup,
+                          pack_edges=args.pack_edges)
     serve = None
     if rank == 0 and not args.no_serve:
         serve = serve_leg(args.serve_requests or 256, args.serve_pool or 32)
