@@ -76,6 +76,35 @@ def dist_env():
     return rank, world, local
 
 
+# Replicas: with N > 1 every rank counts its own copy of the workload on its own GPU.  The
+# counts need no exchange; the ranks only meet at barriers around the timed region and to
+# take the slowest rank's time.  A gloo group carries those few host-side messages.
+
+def init_replicas(world):
+    """The process group of the replicas (None for one process)."""
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group("gloo")
+    return dist
+
+
+def max_over_ranks(pg, x):
+    """The largest value of x over all ranks (x itself for one process)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, steps, units_per_step, max_ms):
+    """Whole-job throughput: units all ranks processed over the slowest rank's time."""
+    return world * steps * units_per_step / (max_ms / 1e3)
+
+
 # --------------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -563,11 +592,7 @@ def run_batch_only(args, rank, world, local):
     """--workload batch: the batched leg alone at its full size, as the JSON line's metric."""
     import torch
     torch.cuda.set_device(local)
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
-        pg = dist
+    pg = init_replicas(world)
     count = args.batch_graphs or 4096
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get(
         "CUDA_VISIBLE_DEVICES") else str(local)
@@ -575,14 +600,10 @@ def run_batch_only(args, rank, world, local):
     clocks.start()
     leg = batch_leg(count, args.steps, args.warmup, pack_edges=args.pack_edges)
     clk = clocks.stop()
-    ms = leg["batched"]["ms"]
-    if pg:
-        t = torch.tensor([ms], dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(pg, leg["batched"]["ms"])
     if rank == 0:
         b = leg["batched"]
-        line = {"metric": "batched graphs/s", "value": world * count / (ms / 1e3), "unit": "graphs/s",
+        line = {"metric": "batched graphs/s", "value": replica_throughput(world, 1, count, ms), "unit": "graphs/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
                 "data": "synthetic",
@@ -637,11 +658,7 @@ def run_gpu(args, rank, world, local):
     if args.workload == "serve":
         return run_serve_only(args, rank, world, local)
     torch.cuda.set_device(local)
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
-        pg = dist
+    pg = init_replicas(world)
     spec = W.SINGLE[args.workload]
     s, d = spec.edges()
     m_in = len(s)
@@ -691,13 +708,10 @@ def run_gpu(args, rank, world, local):
     t_wall = time.perf_counter() - t_wall0
     launches = tc.kernel_launches() - l0
     clk = clocks.stop()
-    total_ms = sum(x[0] for x in steps)
+    total_ms = max_over_ranks(pg, sum(x[0] for x in steps))
     if pg:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
         pg.barrier()
-    value = world * args.steps * m_hat / (total_ms / 1e3)
+    value = replica_throughput(world, args.steps, m_hat, total_ms)
     build_ms = statistics.mean(x[1] for x in steps)
     count_ms = statistics.mean(x[2] for x in steps)
     kernel_ms = statistics.mean(x[3] for x in steps)
@@ -720,12 +734,8 @@ def run_gpu(args, rank, world, local):
                 raise RuntimeError("count changed in the e2e run")
             return e0.elapsed_time(e1)
         host_step()
-        e2e_ms = sum(host_step() for _ in range(args.steps))
-        if pg:
-            t = torch.tensor([e2e_ms], dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": world * args.steps * m_hat / (e2e_ms / 1e3), "unit": UNIT,
+        e2e_ms = max_over_ranks(pg, sum(host_step() for _ in range(args.steps)))
+        e2e = {"value": replica_throughput(world, args.steps, m_hat, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": 8 * m_in, "d2h_bytes_per_step": 8,
                "ms_per_step": e2e_ms / args.steps}
 
