@@ -51,3 +51,51 @@ def test_full_size_total_and_sampled_edges(name):
             assert int(pe_h[i]) == len(np.intersect1d(a, b, assume_unique=True)), (v, u)
         T3, tv = g.count_per_vertex()
         assert T3 == T and int(tv.sum().item()) == 3 * T
+
+
+def _spread(specs, k):
+    """k specs spread over the list (the workload's range of sizes), smallest input first."""
+    step = max(1, len(specs) // k)
+    return sorted(specs[::step][:k], key=lambda sp: sp.num_input_edges)
+
+
+@pytest.mark.parametrize("options", [{}, dict(small_max=128, warps_per_block=16, big_warps=8, piece=2048)])
+def test_batch_workload_sample(options):
+    """Every 16th graph of the 4096-graph batch workload, in packs of at most 2^29 input edges
+    as the bench builds them: each total equals the graph counted alone, and sampled graphs
+    equal the oracle."""
+    specs = W.batch_specs()[::16]
+    graphs = [sp.edges() + (sp.n,) for sp in specs]
+    opt = tc.default_options(**options)
+    with tc.Batch.build(graphs, options=opt, pack_edges=1 << 29) as b:
+        totals = b.count()
+        edges = b.graph_edges()
+    for j, (s, d, n) in enumerate(graphs):
+        with tc.Graph.build(s, d, n, opt) as g:
+            assert g.count() == int(totals[j]), j
+            assert g.info()["m_hat"] == int(edges[j])
+    for sp in _spread(specs, 6):
+        j = specs.index(sp)
+        s, d, n = graphs[j]
+        assert oracle.count(oracle.oriented_csr(oracle.simple_graph(n, s, d)), threads=THREADS) == int(totals[j]), j
+
+
+def test_serve_workload_sample():
+    """The first 24 graphs of the serving pool, served by 4 slots with grouping: every total
+    equals the graph counted alone, and the smaller ones equal the oracle."""
+    specs = [W.serve_spec(j) for j in range(24)]
+    graphs = [(torch.from_numpy(s).pin_memory(), torch.from_numpy(d).pin_memory(), sp.n)
+              for sp in specs for s, d in [sp.edges()]]
+    with tc.Server(60 << 30, slots=4) as sv:
+        for j, (s, d, n) in enumerate(graphs):
+            sv.submit(s, d, n, tag=j)
+        sv.drain(600_000)
+        res = {r["tag"]: r for r in sv.poll(100)}
+    assert sorted(res) == list(range(len(graphs)))
+    for j, (s, d, n) in enumerate(graphs):
+        assert res[j]["status"] == 0
+        with tc.Graph.build(s, d, n) as g:
+            assert g.count() == res[j]["total"], j
+        if specs[j].num_input_edges <= 4_000_000:
+            want = oracle.count(oracle.oriented_csr(oracle.simple_graph(n, s.numpy(), d.numpy())), threads=THREADS)
+            assert want == res[j]["total"], j
