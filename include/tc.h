@@ -256,6 +256,10 @@ tc_status tc_vertex_cost(tc_graph_t g, int32_t fn, tc_stream_t stream, uint64_t*
  *            list's [first, last] range).  Counting adds one atomic per warp batch.
  * With trace != NULL the call synchronises `stream` before returning.
  */
+/* Partner lists of big owners with at least this many entries are trimmed to the owner
+ * list's [first, last] range before they are probed; shorter ones are probed whole. */
+#define TC_TRIM_MIN_ENTRIES 16
+
 typedef struct tc_count_trace {
     uint64_t* chunks;
     int64_t cap;

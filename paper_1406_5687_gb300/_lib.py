@@ -24,6 +24,7 @@ TC_COST_EDGE, TC_COST_MERGE, TC_COST_ONE, TC_COST_DEGREE, TC_COST_PATRIC, TC_COS
 TC_FN_ONE, TC_FN_DEGREE, TC_FN_PATRIC, TC_FN_NEW = range(4)
 TC_INPUT_SANITIZE, TC_INPUT_STRICT = 0, 1
 TC_COUNT_STATIC_MAX_TASKS = 1 << 19  # include/tc.h
+TC_TRIM_MIN_ENTRIES = 16  # include/tc.h
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)

@@ -35,7 +35,10 @@ namespace tcg {
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kHashMul = 0x9E3779B1u;  // Knuth's multiplicative constant, 2^32 / golden ratio
-constexpr int kUnits = 4;  // 16-byte units of partner lists a lane loads per step of warp_batch_count
+#ifndef TC_UNITS
+#define TC_UNITS 4
+#endif
+constexpr int kUnits = TC_UNITS;  // 16-byte units of partner lists a lane loads per step of warp_batch_count
 
 struct CountArgs {
     const int64_t* off;
@@ -230,10 +233,16 @@ __device__ __forceinline__ HashView region_view(uint32_t* tbl, uint32_t reg) {
 // Both lists are ascending, so only the partner entries within [omin, omax] (the owner
 // list's first and last entry) can be in the owner's list: shrink the partner list
 // cols[ps, ps + len) to that sub-list.  The two bounds are found by binary searches run
-// side by side; lists already inside the range (the usual case) cost two loads.
+// side by side; lists already inside the range (the usual case) cost two loads.  Lists
+// shorter than kTrimMin are left whole.
+#ifndef TC_TRIM_MIN
+#define TC_TRIM_MIN TC_TRIM_MIN_ENTRIES
+#endif
+constexpr uint32_t kTrimMin = TC_TRIM_MIN;  // shorter partner lists are read whole: a search would cost about as much
+
 __device__ __forceinline__ void trim_to_range(const int32_t* __restrict__ cols, uint32_t& ps, uint32_t& len,
                                               uint32_t omin, uint32_t omax) {
-    if (len == 0u) return;
+    if (len < kTrimMin) return;
     const uint32_t first = (uint32_t)__ldg(&cols[ps]), last = (uint32_t)__ldg(&cols[ps + len - 1u]);
     if (first >= omin && last <= omax) return;
     if (last < omin || first > omax) {

@@ -360,10 +360,13 @@ def test_tiny_wait_limits_fail_cleanly_or_count_exactly():
         assert g.count() == want
 
 
-def _streamed_entries(csr, small_max, piece):
+def _streamed_entries(csr, small_max, piece, trim_min=None):
     """Partner entries each class's kernel must read: a small owner's partner list whole;
     for a big owner, per piece of its list (pieces of `piece` entries), the part of the
-    partner list within the piece's [first, last] entries (both lists are ascending)."""
+    partner list within the piece's [first, last] entries (both lists are ascending) when the
+    partner list has at least trim_min entries, else the whole list."""
+    from paper_1406_5687_gb300 import _lib
+    trim_min = _lib.TC_TRIM_MIN_ENTRIES if trim_min is None else trim_min
     own, par, ns = oracle.tasks(csr, small_max=small_max, with_split=True)
     off, cols = csr.off, csr.cols.astype(np.int64)
     dh = np.diff(off)
@@ -380,7 +383,8 @@ def _streamed_entries(csr, small_max, piece):
         pm = p[m]
         lo = np.searchsorted(key, pm * (1 << 32) + lo_v, side="left")
         hi = np.searchsorted(key, pm * (1 << 32) + hi_v, side="right")
-        big += int((hi - lo).sum())
+        whole = dh[pm] < trim_min
+        big += int(np.where(whole, dh[pm], hi - lo).sum())
     return small, big
 
 
