@@ -399,3 +399,19 @@ def test_streamed_entries_match_the_host_count(name, piece):
         assert tuple(meta["streamed"]) == want
         _, meta2, _, _ = g.count_ex(tc.default_options(piece=piece), timing=True)
         assert list(meta2["streamed"]) == [-1, -1]
+
+
+@pytest.mark.parametrize("shift", [0, 1, 2, 3, 4])
+def test_unaligned_and_ragged_device_edge_lists(shift):
+    """Edge lists that start off a 16-byte boundary, or whose length is not a multiple of 4,
+    take the canonicalize kernel's scalar path; the count is the same."""
+    n, s, d = GRAPHS["ba_30k"]
+    want = oracle.count(oracle_csr(n, s[shift:len(s) - shift], d[shift:len(d) - shift]))
+    sd, dd = torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda()
+    with tc.Graph.build(sd[shift:len(s) - shift], dd[shift:len(d) - shift], n) as g:
+        assert g.count() == want
+    bad = dd.clone()
+    bad[len(d) - 1 - shift] = n  # an out-of-range id in the ragged tail
+    with pytest.raises(tc.TcError) as e:
+        tc.Graph.build(sd[shift:len(s) - shift], bad[shift:len(d) - shift], n)
+    assert e.value.code == tc._lib.TC_ERR_VERTEX_RANGE
