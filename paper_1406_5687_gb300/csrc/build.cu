@@ -208,13 +208,33 @@ __global__ void k_max_deg(const int32_t* __restrict__ deg, const int32_t* __rest
 }
 
 // --------------------------------------------------------------------------- tasks
-// Task key: partner in the low 32 bits, then owner (b bits), class (1 when the owner's list
-// has more than small_max entries) and a drop bit (partner list empty).  The stable sort on
-// the drop/class/owner bits alone keeps each owner's tasks in the order of their oriented
-// edges in the N+ lists, puts every small task first and every dropped edge last.
+// Owners are renumbered so that the task order (class, owner, position) becomes an order on
+// one number: small-class vertices (list of at most small_max entries) first, then the big
+// ones, each in id order; a dropped task (partner list empty) gets n and sorts last.  With
+// n <= 2^24 the sort key is 24 bits (three digit passes).
+struct BigVal {
+    const int32_t* dhat;
+    int small_max;
+    __device__ uint64_t operator()(int64_t v) const { return dhat[v] > small_max ? 1ull : 0ull; }
+};
+
+// rid[v] = v's number; inv[rid[v]] = v.  big_excl: exclusive prefix of the big flags (n + 1).
+__global__ void k_renumber(const int32_t* __restrict__ dhat, int small_max, const uint64_t* __restrict__ big_excl,
+                           int32_t n, uint32_t* __restrict__ rid, uint32_t* __restrict__ inv) {
+    const uint32_t ns = (uint32_t)((uint64_t)n - big_excl[n]);
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t be = (uint32_t)big_excl[v];
+        const uint32_t r = dhat[v] > small_max ? ns + be : (uint32_t)v - be;
+        rid[v] = r;
+        inv[r] = (uint32_t)v;
+    }
+}
+
+// Task key: partner in the low 32 bits, the owner's number above.  The stable sort on the
+// number alone keeps each owner's tasks in the order of their oriented edges in the lists.
 __global__ void k_task_keys(const uint64_t* __restrict__ okeys, const int32_t* __restrict__ cols, int64_t mh, int b,
-                            const int32_t* __restrict__ dhat, int small_max, uint64_t* __restrict__ tkeys,
-                            BuildCounters* cnt) {
+                            const int32_t* __restrict__ dhat, int small_max, const uint32_t* __restrict__ rid,
+                            int32_t n, uint64_t* __restrict__ tkeys, BuildCounters* cnt) {
     const int lane = threadIdx.x & 31;
     unsigned long long sv = 0, su = 0, ss = 0, nt = 0, nsm = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mh; i += (int64_t)gridDim.x * blockDim.x) {
@@ -226,14 +246,15 @@ __global__ void k_task_keys(const uint64_t* __restrict__ okeys, const int32_t* _
         sv += (unsigned long long)dv;
         su += (unsigned long long)du;
         const int32_t dop = dv >= du ? dv : du;
-        const uint64_t big = dop > small_max ? 1ull : 0ull;
-        const uint64_t drop = dp > 0 ? 0ull : 1ull;
+        const bool big = dop > small_max;
+        uint64_t num = (uint64_t)(uint32_t)n;
         if (dp > 0) {
             ss += (unsigned long long)dp;
             nt += 1;
-            nsm += 1ull - big;
+            nsm += big ? 0ull : 1ull;
+            num = rid[o];
         }
-        tkeys[i] = (drop << (33 + b)) | (big << (32 + b)) | ((uint64_t)o << 32) | p;
+        tkeys[i] = (num << 32) | p;
     }
     sv = warp_sum(sv);
     su = warp_sum(su);
@@ -263,12 +284,11 @@ struct OwnerStartVal {
     __device__ uint32_t operator()(int64_t i) const { return (uint32_t)(Ts + i); }
 };
 
-__global__ void k_task_records(const uint64_t* __restrict__ tkeys, int64_t T, int b, const int64_t* __restrict__ off,
-                               TaskRec* __restrict__ rec) {
-    const uint64_t mask = (1ull << b) - 1;
+__global__ void k_task_records(const uint64_t* __restrict__ tkeys, int64_t T, const uint32_t* __restrict__ inv,
+                               const int64_t* __restrict__ off, TaskRec* __restrict__ rec) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
         uint64_t k = tkeys[t];
-        uint32_t o = (uint32_t)((k >> 32) & mask), p = (uint32_t)(k & 0xFFFFFFFFu);
+        uint32_t o = inv[(uint32_t)(k >> 32)], p = (uint32_t)(k & 0xFFFFFFFFu);
         int64_t s = off[p], e = off[p + 1];
         TaskRec r;
         r.owner = o;
@@ -305,7 +325,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     Allocator* al = &g->al;
     const long long spin = g->opt.retry_limit > 0 ? g->opt.retry_limit : (1ll << 20);
     const int b = bits_for(n);
-    if (b > 30) return TC_ERR_UNSUPPORTED;  // task keys hold 32 + b + 2 bits
+    if (b > 30) return TC_ERR_UNSUPPORTED;  // edge keys hold 2b bits, task keys 32 + bits(n)
     const int nbits = 2 * b;
     const uint64_t sent = (nbits >= 64) ? ~0ull : ((1ull << nbits) - 1);
     g->n = n;
@@ -403,14 +423,25 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     TC_CUDA_TRY(cudaGetLastError());
 
     // tasks
+    DevBuf<uint32_t> rid, inv;
+    TC_TRY(rid.alloc(al, (size_t)(n > 0 ? n : 1), s));
+    TC_TRY(inv.alloc(al, (size_t)(n > 0 ? n : 1), s));
+    if (n > 0) {
+        DevBuf<uint64_t> bex, scr;
+        TC_TRY(bex.alloc(al, (size_t)n + 1, s));
+        TC_TRY(scr.alloc(al, scan_scratch_words(n), s));
+        TC_CUDA_TRY(scan_exclusive(BigVal{dhat.ptr, g->opt.small_max}, n, bex.ptr, scr.ptr, s));
+        k_renumber<<<grid_stride_blocks(n), kThreads, 0, s>>>(dhat.ptr, g->opt.small_max, bex.ptr, n, rid.ptr, inv.ptr);
+        note_launch();
+    }
     if (mh > 0) {
         k_task_keys<<<grid_stride_blocks(mh), kThreads, 0, s>>>(osorted, cols.ptr, mh, b, dhat.ptr,
-                                                                g->opt.small_max, free_buf, cnt.ptr);
+                                                                g->opt.small_max, rid.ptr, n, free_buf, cnt.ptr);
         note_launch();
     }
     TC_CUDA_TRY(cudaGetLastError());
     uint64_t* tsorted = nullptr;
-    TC_TRY(radix_sort_u64(free_buf, osorted, mh, 32, b + 2, al, s, &tsorted, g->status, spin));
+    TC_TRY(radix_sort_u64(free_buf, osorted, mh, 32, bits_for(n + 1), al, s, &tsorted, g->status, spin));
     TC_TRY(check_device_error(g, s));
     TC_CUDA_TRY(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(hc), cudaMemcpyDeviceToHost, s));
     TC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -418,7 +449,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     DevBuf<TaskRec> rec;
     TC_TRY(rec.alloc(al, T > 0 ? T : 1, s));
     if (T > 0) {
-        k_task_records<<<grid_stride_blocks(T), kThreads, 0, s>>>(tsorted, T, b, off.ptr, rec.ptr);
+        k_task_records<<<grid_stride_blocks(T), kThreads, 0, s>>>(tsorted, T, inv.ptr, off.ptr, rec.ptr);
         note_launch();
     }
     TC_CUDA_TRY(cudaGetLastError());
