@@ -38,7 +38,8 @@ constexpr uint32_t kHashMul = 0x9E3779B1u;  // Knuth's multiplicative constant, 
 #ifndef TC_UNITS
 #define TC_UNITS 4
 #endif
-constexpr int kUnits = TC_UNITS;  // 16-byte units of partner lists a lane loads per step of warp_batch_count
+constexpr int kUnits = TC_UNITS;
+constexpr int kTvCacheLog = 11;  // 2048 (vertex, count) slots per block for per-vertex counts  // 16-byte units of partner lists a lane loads per step of warp_batch_count
 
 struct CountArgs {
     const int64_t* off;
@@ -67,6 +68,8 @@ struct CountArgs {
     long long n_owners;         // big class: owners
     const int64_t* gtask;       // packs: this class's first task of each graph, then its end
     unsigned long long* streamed;  // traced counts only: partner entries read, summed per class
+    int cache_log;                 // per-vertex counts: log2 slots of the block's T_v cache (0: none)
+    int cache_off;                 // its offset in the block's dynamic shared memory, in words
     long long n_sub;            // packs: graphs (0: one graph, one total)
 };
 
@@ -116,20 +119,77 @@ __device__ __forceinline__ long long edge_position(const CountArgs& a, uint32_t 
     return lo;
 }
 
-template <bool EXTRA>
-__device__ __forceinline__ void on_hit(const CountArgs& a, uint32_t owner, uint32_t partner, uint32_t w) {
-    if (!EXTRA) return;
-    if (a.t_v) {
-        atomicAdd(&a.t_v[owner], 1ull);
-        atomicAdd(&a.t_v[partner], 1ull);
-        atomicAdd(&a.t_v[w], 1ull);
+// The block's dynamic shared memory: hash tables, then (per-vertex counts) the T_v cache.
+extern __shared__ uint32_t smem_dyn[];
+
+// Hub vertices close a great many triangles, and global atomics on one address serialise.
+// A block therefore keeps a small direct-mapped cache of (vertex, count) in shared memory:
+// a vertex takes a free slot on its first increment and later ones add there; a vertex
+// whose slot is taken goes to global memory.  The block adds the cache to T_v at its end.
+__device__ __forceinline__ void add_tv(const CountArgs& a, uint32_t w) {
+    if (a.cache_log) {
+        uint32_t* tags = smem_dyn + a.cache_off;
+        uint32_t* cnts = tags + (1u << a.cache_log);
+        const uint32_t sl = (w * kHashMul) >> (32 - a.cache_log);
+        uint32_t t = tags[sl];
+        if (t == kEmpty) t = atomicCAS(&tags[sl], kEmpty, w);
+        if (t == w || t == kEmpty) {
+            atomicAdd(&cnts[sl], 1u);
+            return;
+        }
     }
-    if (a.per_edge) {
-        // the oriented edge runs from whichever endpoint comes first in the degree order
-        const int32_t dox = a.deg[owner], dpx = a.deg[partner];
-        const bool owner_first = dox < dpx || (dox == dpx && owner < partner);
-        const uint32_t v = owner_first ? owner : partner, u = owner_first ? partner : owner;
-        atomicAdd(&a.per_edge[edge_position(a, v, u)], 1u);
+    atomicAdd(&a.t_v[w], 1ull);
+}
+
+__device__ __forceinline__ void tv_cache_init(const CountArgs& a) {
+    if (!a.cache_log) return;
+    uint32_t* tags = smem_dyn + a.cache_off;
+    for (uint32_t i = threadIdx.x; i < (1u << a.cache_log); i += blockDim.x) {
+        tags[i] = kEmpty;
+        tags[i + (1u << a.cache_log)] = 0u;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void tv_cache_flush(const CountArgs& a) {
+    if (!a.cache_log) return;
+    __syncthreads();
+    const uint32_t* tags = smem_dyn + a.cache_off;
+    for (uint32_t i = threadIdx.x; i < (1u << a.cache_log); i += blockDim.x) {
+        const uint32_t c = tags[i + (1u << a.cache_log)];
+        if (tags[i] != kEmpty && c) atomicAdd(&a.t_v[tags[i]], (unsigned long long)c);
+    }
+}
+
+// Per-vertex and per-edge outputs.  Every hit w of a task (owner, partner) adds 1 to T_w;
+// the task's own vertices and its oriented edge gain the task's hits, which the warp sums
+// per task before one atomic each (flush_task_hits).
+__device__ __forceinline__ long long oriented_edge_position(const CountArgs& a, uint32_t owner, uint32_t partner) {
+    // the oriented edge runs from whichever endpoint comes first in the degree order
+    const int32_t dox = a.deg[owner], dpx = a.deg[partner];
+    const bool owner_first = dox < dpx || (dox == dpx && owner < partner);
+    return edge_position(a, owner_first ? owner : partner, owner_first ? partner : owner);
+}
+
+// Lanes holding units of the same task carry the same key and are adjacent: a segmented
+// suffix sum leaves each task's hits in its first lane, which adds them once.
+__device__ __forceinline__ void flush_task_hits(const CountArgs& a, uint32_t h, int key, uint32_t owner, uint32_t partner,
+                                                long long epos, int lane) {
+    uint32_t sum = h;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_down_sync(kFull, sum, o);
+        const int tk = __shfl_down_sync(kFull, key, o);
+        if (lane + o < 32 && tk == key) sum += t;
+    }
+    const int pk = __shfl_up_sync(kFull, key, 1);
+    const bool head = lane == 0 || pk != key;
+    if (head && key < 32 && sum != 0u) {
+        if (a.t_v) {
+            atomicAdd(&a.t_v[owner], (unsigned long long)sum);
+            atomicAdd(&a.t_v[partner], (unsigned long long)sum);
+        }
+        if (a.per_edge) atomicAdd(&a.per_edge[epos], sum);
     }
 }
 
@@ -315,6 +375,8 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
         const uint32_t tot = warp_sum(len);
         if (lane == 0 && tot) atomicAdd(a.streamed, (unsigned long long)tot);
     }
+    long long epos = 0;
+    if (EXTRA && a.per_edge && len != 0u) epos = oriented_edge_position(a, r.owner, r.partner);
     const uint32_t units = len != 0u ? (((ps & 3u) + len + 3u) >> 2) : 0u;
     const uint32_t uincl = warp_inclusive_scan(units, lane);
     const uint32_t ustart = uincl - units;
@@ -324,6 +386,8 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
         int4 v[kUnits];
         uint32_t lo[kUnits], ln[kUnits], e0[kUnits], rg[kUnits];
         uint32_t ow[kUnits], pa[kUnits];
+        long long ep[kUnits];
+        int qk[kUnits];
         bool in[kUnits];
 #pragma unroll
         for (int u = 0; u < kUnits; ++u) {
@@ -337,12 +401,14 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
             ln[u] = __shfl_sync(kFull, len, q);
             rg[u] = __shfl_sync(kFull, reg, q);
             const uint32_t us = __shfl_sync(kFull, ustart, q);
+            const uint32_t unit = wb + (uint32_t)lane;
+            in[u] = unit < U;
             if (EXTRA) {
                 ow[u] = __shfl_sync(kFull, r.owner, q);
                 pa[u] = __shfl_sync(kFull, r.partner, q);
+                ep[u] = __shfl_sync(kFull, epos, q);
+                qk[u] = in[u] ? q : 32 + lane;
             }
-            const uint32_t unit = wb + (uint32_t)lane;
-            in[u] = unit < U;
             e0[u] = (lo[u] & ~3u) + 4u * (unit - us);
             v[u] = in[u] ? __ldg(reinterpret_cast<const int4*>(a.cols + e0[u])) : make_int4(-1, -1, -1, -1);
         }
@@ -363,12 +429,15 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
                     cnt += hash_probe_rest(hv, xs[k], (hash_start(hv, xs[k]) + 2) & hv.cmask) ? 1u : 0u;
                 }
             } else {
+                uint32_t h = 0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const bool hit = ok[k] && hash_probe(hv, xs[k]);
-                    cnt += hit ? 1u : 0u;
-                    if (hit) on_hit<EXTRA>(a, ow[u], pa[u], xs[k]);
+                    h += hit ? 1u : 0u;
+                    if (hit && a.t_v) add_tv(a, xs[k]);
                 }
+                cnt += h;
+                flush_task_hits(a, h, qk[u], ow[u], pa[u], ep[u], lane);
             }
         }
     }
@@ -760,33 +829,36 @@ __device__ __forceinline__ void worker_epilogue(const CountArgs& a, unsigned lon
 // Small owners: one worker per block, a table per warp.
 template <bool EXTRA>
 __global__ void __launch_bounds__(512, 2) k_count_small(CountArgs a) {
-    extern __shared__ uint32_t smem_tbl[];
     __shared__ unsigned s_claim;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* tbl = smem_tbl + (size_t)warp * a.table_slots;
+    uint32_t* tbl = smem_dyn + (size_t)warp * a.table_slots;
     unsigned long long acc = 0;
     long long busy = 0, nch = 0;
+    if (EXTRA) tv_cache_init(a);
     block_worker(a, [&](long long t0, long long t1) {
         by_graph<EXTRA>(a, t0, t1, [&](long long u0, long long u1) { process_small_block<EXTRA>(a, u0, u1, tbl, &s_claim, lane, acc); },
                  acc, lane, warp);
     }, lane, warp, busy, nch);
+    if (EXTRA) tv_cache_flush(a);
     worker_epilogue<EXTRA>(a, acc, lane, busy, nch);
 }
 
 // Big owners: one worker per block, one table per block.
 template <bool EXTRA>
 __global__ void __launch_bounds__(512, 2) k_count_big(CountArgs a) {
-    extern __shared__ uint32_t smem_tbl[];
+    uint32_t* smem_tbl = smem_dyn;
     __shared__ BigWindow s_win;
     __shared__ unsigned s_next;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long acc = 0;
     long long busy = 0, nch = 0;
+    if (EXTRA) tv_cache_init(a);
     block_worker(a, [&](long long t0, long long t1) {
         by_graph<EXTRA>(a, t0, t1, [&](long long u0, long long u1) {
             process_big<EXTRA>(a, u0, u1, smem_tbl, &s_win, &s_next, lane, warp, acc);
         }, acc, lane, warp);
     }, lane, warp, busy, nch);
+    if (EXTRA) tv_cache_flush(a);
     worker_epilogue<EXTRA>(a, acc, lane, busy, nch);
 }
 
@@ -946,10 +1018,14 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     const int threads_b = opt.big_warps * 32;
     const int slots_b = 8 * opt.piece;
     const size_t smem_b = (size_t)slots_b * sizeof(uint32_t);
+    // per-vertex counts: a T_v cache of 2^kTvCacheLog (vertex, count) slots after the tables
+    const int cache_log = t_v ? kTvCacheLog : 0;
+    const size_t cache_bytes = cache_log ? ((size_t)2 << cache_log) * sizeof(uint32_t) : 0;
+    const size_t smem_s_x = smem_s + cache_bytes, smem_b_x = smem_b + cache_bytes;
     int blocks_s = 0, blocks_b = 0;
     if (extra) {
-        TC_TRY(grid_for_kernel(k_count_small<true>, wpb * 32, smem_s, opt.blocks_per_sm, &blocks_s));
-        TC_TRY(grid_for_kernel(k_count_big<true>, threads_b, smem_b, opt.blocks_per_sm, &blocks_b));
+        TC_TRY(grid_for_kernel(k_count_small<true>, wpb * 32, smem_s_x, opt.blocks_per_sm, &blocks_s));
+        TC_TRY(grid_for_kernel(k_count_big<true>, threads_b, smem_b_x, opt.blocks_per_sm, &blocks_b));
     } else {
         TC_TRY(grid_for_kernel(k_count_small<false>, wpb * 32, smem_s, opt.blocks_per_sm, &blocks_s));
         TC_TRY(grid_for_kernel(k_count_big<false>, threads_b, smem_b, opt.blocks_per_sm, &blocks_b));
@@ -996,7 +1072,9 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     a.n_owners = g->owners_big;
     a.n_sub = g->n_sub;
     const bool count_streamed = trace && trace->count_streamed;
+    a.cache_log = cache_log;
     // small class
+    a.cache_off = wpb * slots_s;
     a.gtask = g->sub_task;
     a.streamed = count_streamed ? &w.sched[0].streamed : nullptr;
     a.t_begin = 0;
@@ -1009,13 +1087,14 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     a.warps_per_block = wpb;
     a.busy_offset = 0;
     if (Ts > 0) {
-        if (extra) k_count_small<true><<<blocks_s, wpb * 32, smem_s, s>>>(a);
+        if (extra) k_count_small<true><<<blocks_s, wpb * 32, smem_s_x, s>>>(a);
         else k_count_small<false><<<blocks_s, wpb * 32, smem_s, s>>>(a);
         note_launch();
         TC_CUDA_TRY(cudaGetLastError());
     }
     if (trace) TC_CUDA_TRY(cudaEventRecord(ev[2], s));
     // big class
+    a.cache_off = slots_b;
     a.gtask = g->sub_task ? g->sub_task + (g->n_sub + 1) : nullptr;
     a.streamed = count_streamed ? &w.sched[1].streamed : nullptr;
     a.t_begin = Ts;
@@ -1027,7 +1106,7 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     a.warps_per_block = opt.big_warps;
     a.busy_offset = W_s;
     if (T > Ts) {
-        if (extra) k_count_big<true><<<blocks_b, threads_b, smem_b, s>>>(a);
+        if (extra) k_count_big<true><<<blocks_b, threads_b, smem_b_x, s>>>(a);
         else k_count_big<false><<<blocks_b, threads_b, smem_b, s>>>(a);
         note_launch();
         TC_CUDA_TRY(cudaGetLastError());
@@ -1146,6 +1225,8 @@ static tc_status count_enqueue_static(tc_graph* g, cudaStream_t s, unsigned long
     a.n_owners = g->owners_big;
     a.gtask = nullptr;
     a.streamed = nullptr;
+    a.cache_log = 0;
+    a.cache_off = 0;
     a.n_sub = 0;
     a.t_begin = 0;
     a.t_end = Ts;
