@@ -57,7 +57,12 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain leg")
     p.add_argument("--no-serve", action="store_true", help="skip the serving-vs-plain leg")
+    p.add_argument("--no-per-vertex", action="store_true",
+                   help="skip the per-vertex / per-edge / clustering timings of the optional outputs")
     p.add_argument("--pack-edges", type=int, default=0, help="input edges per batch pack (0: the library default)")
+    p.add_argument("--ablation", action="store_true",
+                   help="count the workload under every cost model and static share of Eq. 1 and print one "
+                        "JSON line per setting (kernel times and per-worker idle spread)")
     p.add_argument("--serve-requests", type=int, default=0,
                    help="requests of the serving window (default: 256 as a leg of a single-graph run, 2000 "
                         "with --workload serve)")
@@ -647,11 +652,56 @@ def run_serve_only(args, rank, world, local):
     return 0
 
 
+COST_MODELS = ["edge", "merge", "one", "degree", "patric", "new"]
+
+
+def run_ablation(args, local):
+    """Cost functions (Sec. IV-B, IV-F, V-A) and the static share of Eq. 1 on the GPU: the same
+    built graph counted under each setting; per class, the kernel time and the spread of the
+    workers' busy clocks (the idle time of Sec. V-E: max busy vs median busy)."""
+    import numpy as np
+    import torch
+    import paper_1406_5687_gb300 as tc
+    from graphgen import workloads as W
+    torch.cuda.set_device(local)
+    spec = W.SINGLE[args.workload]
+    s, d = spec.edges()
+    g = tc.Graph.build(torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), spec.n)
+    T_ref = g.count()
+    for model in range(6):
+        for sp in (0, 50, 100):
+            opt = tc.default_options(cost_model=model, static_percent=sp)
+            best = None
+            for _ in range(max(2, args.steps)):
+                T, meta, _, busy = g.count_ex(opt, busy=True)
+                if T != T_ref:
+                    raise RuntimeError("the count changed with the cost model")
+                if best is None or meta["kernel_ms"] < best[0]["kernel_ms"]:
+                    best = (meta, busy.cpu().numpy())
+            meta, b = best
+            ws = meta["n_workers"][0]
+            row = {"workload": WORKLOAD_TEXT[args.workload], "cost_model": COST_MODELS[model], "static_percent": sp,
+                   "kernel_small_ms": meta["kernel_small_ms"], "kernel_big_ms": meta["kernel_big_ms"],
+                   "prefix_ms": meta["prefix_ms"], "chunks": [int(meta["min_chunk"][0]), int(meta["min_chunk"][1])]}
+            for cls, part in (("small", b[:ws]), ("big", b[ws:])):
+                cyc = part[:, 0].astype(np.float64)
+                if len(cyc) and cyc.max() > 0:
+                    row[f"{cls}_busy_max_over_median"] = float(cyc.max() / max(np.median(cyc), 1.0))
+                    row[f"{cls}_idle_fraction"] = float(1.0 - cyc.mean() / cyc.max())
+                    row[f"{cls}_chunks_per_worker"] = float(part[:, 1].mean())
+            print(json.dumps(row), flush=True)
+    g.free()
+    return 0
+
+
 def run_gpu(args, rank, world, local):
     import numpy as np
     import torch
     import paper_1406_5687_gb300 as tc
     from graphgen import workloads as W
+
+    if args.ablation:
+        return run_ablation(args, local) if rank == 0 else 0
 
     if args.workload == "batch":
         return run_batch_only(args, rank, world, local)
@@ -739,6 +789,34 @@ def run_gpu(args, rank, world, local):
                "h2d_bytes_per_step": 8 * m_in, "d2h_bytes_per_step": 8,
                "ms_per_step": e2e_ms / args.steps}
 
+    # the optional outputs of the same count (outside the timed region): per-vertex T_v,
+    # per-edge counts and clustering coefficients, CUDA events on the same stream
+    extras = None
+    if rank == 0 and not args.no_per_vertex:
+        gg = tc.Graph.build(s_dev, d_dev, spec.n, opt)
+        def timed(f):
+            best = None
+            for _ in range(2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = f()
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None or ms < best else best
+            return best, r
+        count_ms1, _ = timed(lambda: gg.count(stream))
+        pv_ms, (T_pv, tv) = timed(lambda: gg.count_per_vertex(stream))
+        pe_ms, (T_pe, _pe) = timed(lambda: gg.count_per_edge(stream))
+        cc_ms, _cc = timed(lambda: gg.clustering(tv, stream))
+        if T_pv != T_ref or T_pe != T_ref or int(tv.sum().item()) != 3 * T_ref:
+            raise RuntimeError("per-vertex or per-edge count disagrees with the total")
+        extras = {"count_ms": count_ms1, "per_vertex_ms": pv_ms, "per_edge_ms": pe_ms, "clustering_ms": cc_ms,
+                  "note": "tc_count, tc_count_per_vertex (T_v), tc_count_per_edge and tc_clustering on the same built "
+                          "graph, each the faster of two runs"}
+        del tv, _pe, _cc
+        gg.free()
+
     peak, peak_kind = measured_peaks()
     # The roofline is that of the dominant kernel, k_count_big (the big class of step a7-a8):
     # its algorithmic bytes over its own average duration, timed with CUDA events on the
@@ -785,7 +863,7 @@ def run_gpu(args, rank, world, local):
                                "note": "m_hat / (cost prefix + schedule + intersection), lists resident"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "work": {"small": alg["small"], "big": alg["big"]}, "wall_s_timed": t_wall,
-                "batch": batch, "serve": serve}
+                "per_vertex": extras, "batch": batch, "serve": serve}
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
