@@ -60,6 +60,9 @@ def parse_args():
     p.add_argument("--no-per-vertex", action="store_true",
                    help="skip the per-vertex / per-edge / clustering timings of the optional outputs")
     p.add_argument("--pack-edges", type=int, default=0, help="input edges per batch pack (0: the library default)")
+    p.add_argument("--partitioned", action="store_true",
+                   help="one graph split over the ranks: every rank builds it and counts its cost-balanced "
+                        "part of the tasks; the partial counts are summed (strong scaling)")
     p.add_argument("--ablation", action="store_true",
                    help="count the workload under every cost model and static share of Eq. 1 and print one "
                         "JSON line per setting (kernel times and per-worker idle spread)")
@@ -103,6 +106,16 @@ def max_over_ranks(pg, x):
     t = torch.tensor([float(x)], dtype=torch.float64)
     pg.all_reduce(t, op=pg.ReduceOp.MAX)
     return float(t.item())
+
+
+def sum_over_ranks(pg, x):
+    """The exact sum of the integer x over all ranks (the one reduction of a partitioned count)."""
+    if pg is None:
+        return int(x)
+    import torch
+    t = torch.tensor([int(x)], dtype=torch.int64)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return int(t.item())
 
 
 def replica_throughput(world, steps, units_per_step, max_ms):
@@ -652,6 +665,71 @@ def run_serve_only(args, rank, world, local):
     return 0
 
 
+def run_partitioned(args, rank, world, local):
+    """One graph counted by all ranks: each builds it (a replica) and counts part `rank` of
+    `world` cost-balanced parts of its tasks (tc_count_partition); one uint64 sum over the ranks
+    gives T.  The work is fixed as ranks are added: strong scaling."""
+    import torch
+    import paper_1406_5687_gb300 as tc
+    from graphgen import workloads as W
+    torch.cuda.set_device(local)
+    pg = init_replicas(world)
+    spec = W.SINGLE[args.workload]
+    s, d = spec.edges()
+    s_dev, d_dev = torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda()
+    del s, d
+    stream = torch.cuda.current_stream()
+    opt = tc.default_options()
+    g0 = tc.Graph.build(s_dev, d_dev, spec.n, opt)
+    T_ref, m_hat = g0.count(stream), g0.info()["m_hat"]
+    g0.free()
+
+    def step():
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        g = tc.Graph.build(s_dev, d_dev, spec.n, opt, stream=stream)
+        e1.record(stream)
+        part = g.count_partition(rank, world, stream)
+        e2.record(stream)
+        e2.synchronize()
+        g.free()
+        return e0.elapsed_time(e2), e0.elapsed_time(e1), e1.elapsed_time(e2), part
+
+    for _ in range(args.warmup):
+        step()
+    if pg:
+        pg.barrier()
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get(
+        "CUDA_VISIBLE_DEVICES") else str(local)
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    l0 = tc.kernel_launches()
+    steps = [step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    launches = tc.kernel_launches() - l0
+    clk = clocks.stop()
+    total_ms = max_over_ranks(pg, sum(x[0] for x in steps))
+    T = sum_over_ranks(pg, steps[-1][3])
+    if pg:
+        pg.barrier()
+    if T != T_ref:
+        raise RuntimeError(f"partial counts sum to {T}, not {T_ref}")
+    if rank == 0:
+        line = {"metric": METRIC, "value": replica_throughput(1, args.steps, m_hat, total_ms), "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD_TEXT[args.workload], "m_hat": m_hat, "triangles": T,
+                           "l2": "inputs larger than L2", "parallelism": f"cost-partitioned over {world} ranks"},
+                "phases_ms": {"build": statistics.mean(x[1] for x in steps),
+                              "count_part": statistics.mean(x[2] for x in steps)},
+                "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
 COST_MODELS = ["edge", "merge", "one", "degree", "patric", "new"]
 
 
@@ -702,6 +780,8 @@ def run_gpu(args, rank, world, local):
 
     if args.ablation:
         return run_ablation(args, local) if rank == 0 else 0
+    if args.partitioned:
+        return run_partitioned(args, rank, world, local)
 
     if args.workload == "batch":
         return run_batch_only(args, rank, world, local)

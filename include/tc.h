@@ -167,6 +167,20 @@ tc_status tc_count(tc_graph_t g, tc_stream_t stream, uint64_t* total);
  */
 tc_status tc_count_async(tc_graph_t g, tc_stream_t stream, uint64_t* total_dev);
 
+/*
+ * Count one part of the graph's tasks, for a count split over several GPUs (each holding a
+ * replica of the graph) or several calls.  Per task class, part p of P takes the tasks whose
+ * exclusive cost prefix lies in [C p / P, C (p + 1) / P) -- Sec. IV-B's cost-balanced
+ * partition, applied to the task costs of a6 -- and schedules them by Eq. 1 + Eq. 2 among
+ * this GPU's workers.  Every task lies in exactly one part, so the sum of the P partial
+ * counts (one uint64 reduction, the MPI_Reduce of Fig. 5) is T.
+ *   part, nparts  0 <= part < nparts.
+ *   partial       host; receives this part's count.
+ * Synchronises `stream`.
+ */
+tc_status tc_count_partition(tc_graph_t g, int32_t part, int32_t nparts, tc_stream_t stream,
+                             uint64_t* partial);
+
 /* Synchronise `stream` and return (and clear) the handle's device error word. */
 tc_status tc_graph_check(tc_graph_t g, tc_stream_t stream);
 

@@ -127,6 +127,13 @@ class Graph:
         _lib.check(load().tc_count(self._h, _stream(stream), ctypes.byref(t)), "tc_count")
         return int(t.value)
 
+    def count_partition(self, part: int, nparts: int, stream=None) -> int:
+        """The count of part `part` of `nparts` cost-balanced parts of the tasks; the parts sum to T."""
+        t = ctypes.c_uint64()
+        _lib.check(load().tc_count_partition(self._h, int(part), int(nparts), _stream(stream), ctypes.byref(t)),
+                   "tc_count_partition")
+        return int(t.value)
+
     def count_async(self, out, stream=None):
         """Enqueue the count; `out` is a CUDA int64 tensor with at least one element."""
         _lib.check(load().tc_count_async(self._h, _stream(stream), ctypes.c_void_p(out.data_ptr())),

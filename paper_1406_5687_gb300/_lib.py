@@ -111,6 +111,7 @@ SIGNATURES = {
     "tc_free": (None, [P]),
     "tc_count": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_uint64)]),
     "tc_count_async": (ctypes.c_int, [P, P, P]),
+    "tc_count_partition": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_uint64)]),
     "tc_graph_check": (ctypes.c_int, [P, P]),
     "tc_count_per_vertex": (ctypes.c_int, [P, P, P, ctypes.POINTER(ctypes.c_uint64)]),
     "tc_count_per_edge": (ctypes.c_int, [P, P, P, ctypes.POINTER(ctypes.c_uint64)]),

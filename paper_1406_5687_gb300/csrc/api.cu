@@ -249,6 +249,17 @@ tc_status tc_count_async(tc_graph_t g, tc_stream_t stream, uint64_t* total_dev) 
     return count_enqueue(g, g->opt, (cudaStream_t)stream, (unsigned long long*)total_dev, nullptr, nullptr, nullptr);
 }
 
+tc_status tc_count_partition(tc_graph_t g, int32_t part, int32_t nparts, tc_stream_t stream, uint64_t* partial) {
+    if (!g || !partial || nparts < 1 || part < 0 || part >= nparts) return TC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last_stream = s;
+    TC_TRY(count_enqueue(g, g->opt, s, g->work.result, nullptr, nullptr, nullptr, part, nparts));
+    unsigned long long r = 0;
+    TC_TRY(read_status(g, s, &r));
+    *partial = r;
+    return TC_OK;
+}
+
 tc_status tc_graph_check(tc_graph_t g, tc_stream_t stream) {
     if (!g) return TC_ERR_INVALID_ARG;
     return read_status(g, (cudaStream_t)stream, nullptr);

@@ -103,7 +103,7 @@ __device__ __forceinline__ long long warp_first_true(long long lo, long long hi,
 // prefix reaches x; x >= C maps to the end of the class.
 __device__ __forceinline__ long long class_bound(const CountArgs& a, unsigned long long x, unsigned long long C,
                                                  unsigned long long base, int lane) {
-    if (x >= C) return a.t_end;
+    if (x >= C && a.sched->at_end) return a.t_end;
     const uint64_t* __restrict__ P = a.P;
     const unsigned long long target = x + base;
     return warp_first_true(a.t_begin, a.t_end, [&](long long q) { return P[q] >= target; }, lane);
@@ -741,7 +741,7 @@ __device__ __forceinline__ void block_worker(const CountArgs& a, Process process
         const unsigned long long q = H / W, r = H % W, w0 = (unsigned long long)wid;
         const unsigned long long lo = w0 * q + (w0 < r ? w0 : r);
         const unsigned long long hi = (w0 + 1) * q + (w0 + 1 < r ? w0 + 1 : r);
-        const long long t0 = wid == 0 ? a.t_begin : class_bound(a, lo, C, base, lane);
+        const long long t0 = wid == 0 && a.sched->at_start ? a.t_begin : class_bound(a, lo, C, base, lane);
         const long long t1 = class_bound(a, hi, C, base, lane);
         if (lane == 0) {
             s_t[0] = t0;
@@ -886,13 +886,20 @@ struct TaskCost {
     }
 };
 
-// Schedule state of both classes: class 0 is tasks [0, Ts), class 1 is [Ts, T).
+// Schedule state of both classes: class 0 is tasks [0, Ts), class 1 is [Ts, T).  With
+// nparts > 1, only part `part` of each class's cost: [Cc part / nparts, Cc (part + 1) / nparts).
 __global__ void k_sched_init(Sched* sc, const uint64_t* P, long long Ts, long long T, long long W0, long long W1,
-                             int static_percent, long long min_chunk) {
+                             int static_percent, long long min_chunk, int part, int nparts) {
     const unsigned long long sp = (unsigned long long)static_percent;
     for (int c = 0; c < 2; ++c) {
-        const unsigned long long base = c == 0 ? 0ull : P[Ts];
-        const unsigned long long C = (c == 0 ? P[Ts] : P[T]) - base;
+        const unsigned long long cbase = c == 0 ? 0ull : P[Ts];
+        const unsigned long long Cc = (c == 0 ? P[Ts] : P[T]) - cbase;
+        // part boundaries without overflow: Cc * p / nparts as (Cc / np) p + ((Cc % np) p) / np
+        const unsigned long long np = (unsigned long long)nparts, p0 = (unsigned long long)part;
+        const unsigned long long lo = (Cc / np) * p0 + ((Cc % np) * p0) / np;
+        const unsigned long long hi = (Cc / np) * (p0 + 1) + ((Cc % np) * (p0 + 1)) / np;
+        const unsigned long long base = cbase + lo;
+        const unsigned long long C = hi - lo;
         const unsigned long long W = (unsigned long long)(c == 0 ? W0 : W1);
         const unsigned long long H = (C / 100ull) * sp + ((C % 100ull) * sp) / 100ull;
         unsigned long long minc = (unsigned long long)min_chunk;
@@ -907,6 +914,8 @@ __global__ void k_sched_init(Sched* sc, const uint64_t* P, long long Ts, long lo
         sc[c].n_chunks = 0;
         sc[c].base = base;
         sc[c].streamed = 0;
+        sc[c].at_start = part == 0 ? 1ull : 0ull;
+        sc[c].at_end = part == nparts - 1 ? 1ull : 0ull;
     }
 }
 
@@ -1004,7 +1013,8 @@ static tc_status grid_for_kernel(K kernel, int threads, size_t smem, int cap_per
 }
 
 tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsigned long long* total_dev,
-                        unsigned long long* t_v, uint32_t* per_edge, tc_count_trace* trace) {
+                        unsigned long long* t_v, uint32_t* per_edge, tc_count_trace* trace, int part, int nparts) {
+    if (nparts < 1 || part < 0 || part >= nparts) return TC_ERR_INVALID_ARG;
     const bool extra = t_v != nullptr || per_edge != nullptr;
     if (g->n_sub > 0 && (extra || trace)) return TC_ERR_UNSUPPORTED;
     TC_TRY(ensure_count_work(g, opt, s));
@@ -1045,7 +1055,7 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     TaskCost tcf{g->trec, T, g->off, w.fcost, opt.cost_model, (uint32_t)opt.piece, (uint32_t)g->opt.small_max,
                  (uint32_t)opt.c_task, (uint32_t)opt.c_owner};
     TC_CUDA_TRY(scan_exclusive(tcf, T, w.prefix, w.scan_scr, s));
-    k_sched_init<<<1, 1, 0, s>>>(w.sched, w.prefix, Ts, T, W_s, W_b, opt.static_percent, opt.min_chunk);
+    k_sched_init<<<1, 1, 0, s>>>(w.sched, w.prefix, Ts, T, W_s, W_b, opt.static_percent, opt.min_chunk, part, nparts);
     note_launch();
     TC_CUDA_TRY(cudaGetLastError());
     TC_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(unsigned long long) * (g->n_sub > 0 ? g->n_sub : 1), s));
@@ -1201,7 +1211,7 @@ static tc_status count_enqueue_static(tc_graph* g, cudaStream_t s, unsigned long
     TaskCost tcf{g->trec, T, g->off, nullptr, opt.cost_model, (uint32_t)opt.piece, (uint32_t)opt.small_max,
                  (uint32_t)opt.c_task, (uint32_t)opt.c_owner};
     TC_CUDA_TRY(scan_exclusive(tcf, T, prefix, scan_scr, s));
-    k_sched_init<<<1, 1, 0, s>>>(sched, prefix, Ts, T, W_s, W_b, opt.static_percent, opt.min_chunk);
+    k_sched_init<<<1, 1, 0, s>>>(sched, prefix, Ts, T, W_s, W_b, opt.static_percent, opt.min_chunk, 0, 1);
     note_launch();
     TC_CUDA_TRY(cudaGetLastError());
     TC_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(unsigned long long), s));

@@ -25,6 +25,8 @@ struct Sched {
     unsigned long long n_chunks;
     unsigned long long base;  // exclusive prefix at the class's first task
     unsigned long long streamed;  // partner-list entries the class's kernel read (traced counts only)
+    unsigned long long at_start;  // 1: this schedule starts at the class's first task (not a later part)
+    unsigned long long at_end;    // 1: it ends at the class's last task
 };
 
 // Device counters written by the build kernels.
@@ -87,8 +89,11 @@ namespace tcg {
 // The count pipeline (count.cu): cost prefix, schedule init, persistent count kernel.
 // Results: total into *total_dev (device uint64), optional t_v (device, n) and per-edge
 // counts (device, m_hat), optional trace.  Enqueue only (no synchronisation).
+// With nparts > 1 only part `part` is counted: per class, the tasks whose exclusive cost
+// prefix lies in [C part / nparts, C (part + 1) / nparts).
 tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsigned long long* total_dev,
-                        unsigned long long* t_v, uint32_t* per_edge, tc_count_trace* trace);
+                        unsigned long long* t_v, uint32_t* per_edge, tc_count_trace* trace, int part = 0,
+                        int nparts = 1);
 
 tc_status ensure_count_work(tc_graph* g, const tc_options& opt, cudaStream_t s);
 

@@ -415,3 +415,37 @@ def test_unaligned_and_ragged_device_edge_lists(shift):
     with pytest.raises(tc.TcError) as e:
         tc.Graph.build(sd[shift:len(s) - shift], bad[shift:len(d) - shift], n)
     assert e.value.code == tc._lib.TC_ERR_VERTEX_RANGE
+
+
+@pytest.mark.parametrize("name", ["cl_200k", "cl_dense", "ba_30k", "k60", "no_edges"])
+@pytest.mark.parametrize("nparts", [1, 2, 3, 7, 64])
+def test_partitioned_count_adds_up(name, nparts):
+    """Cost-balanced parts of the tasks (Sec. IV-B's partition of the a6 costs) cover every
+    task once: the partial counts sum to T."""
+    n, s, d = GRAPHS[name]
+    want = oracle.count(oracle_csr(n, s, d))
+    with tc.Graph.build(s, d, n) as g:
+        parts = [g.count_partition(p, nparts) for p in range(nparts)]
+        assert sum(parts) == want, parts
+        assert g.count() == want  # the full count is unaffected
+
+
+@pytest.mark.parametrize("options", [dict(cost_model=tc.TC_COST_DEGREE), dict(cost_model=tc.TC_COST_NEW),
+                                     dict(static_percent=0), dict(static_percent=100)])
+def test_partitioned_count_with_per_vertex_costs(options):
+    """Per-vertex cost models give zero-cost tasks (an owner's cost sits on its last task), so
+    parts may meet inside an owner's tasks; they still cover every task once."""
+    n, s, d = GRAPHS["cl_200k"]
+    want = oracle.count(oracle_csr(n, s, d))
+    with tc.Graph.build(s, d, n, tc.default_options(**options)) as g:
+        for nparts in (2, 5):
+            assert sum(g.count_partition(p, nparts) for p in range(nparts)) == want
+
+
+def test_partition_arguments():
+    n, s, d = GRAPHS["k3"]
+    with tc.Graph.build(s, d, n) as g:
+        for part, nparts in [(0, 0), (2, 2), (-1, 3)]:
+            with pytest.raises(tc.TcError) as e:
+                g.count_partition(part, nparts)
+            assert e.value.code == tc._lib.TC_ERR_INVALID_ARG

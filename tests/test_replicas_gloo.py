@@ -1,6 +1,7 @@
-"""The multi-GPU path of bench.py is replicas only: every rank counts its own copy of the
-workload, and the ranks meet only to time the slowest one.  These tests run that host-side
-logic as two gloo ranks on the CPU (no GPU is used)."""
+"""The multi-GPU paths of bench.py: replicas (every rank counts its own copy of the workload
+and the ranks meet only to time the slowest one) and a cost-partitioned count (the ranks'
+partial counts are summed once).  These tests run that host-side logic as gloo ranks on the
+CPU (no GPU is used)."""
 import os
 import socket
 import sys
@@ -29,8 +30,9 @@ def _worker(rank, world, port, times, out):
     pg.barrier()
     m = bench.max_over_ranks(pg, times[r])
     v = bench.replica_throughput(w, 5, 1000, m)
+    total = bench.sum_over_ranks(pg, (1 << 40) + r)  # partial counts beyond 32 bits add exactly
     pg.barrier()
-    out.put((r, local, m, v))
+    out.put((r, local, m, v, total))
     pg.destroy_process_group()
 
 
@@ -48,9 +50,10 @@ def test_slowest_rank_sets_the_whole_job_throughput(world):
         p.join(timeout=60)
         assert p.exitcode == 0
     slowest = max(times)
-    for r, local, m, v in res:
+    for r, local, m, v, total in res:
         assert local == r
         assert m == slowest
+        assert total == world * (1 << 40) + sum(range(world))
         # world ranks x 5 steps x 1000 units in the slowest rank's time
         assert v == pytest.approx(world * 5 * 1000 / (slowest / 1e3))
 
@@ -61,3 +64,4 @@ def test_single_process_needs_no_group():
     assert bench.init_replicas(1) is None
     assert bench.max_over_ranks(None, 12.5) == 12.5
     assert bench.replica_throughput(1, 4, 10, 20.0) == pytest.approx(2000.0)
+    assert bench.sum_over_ranks(None, 7) == 7
