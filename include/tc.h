@@ -43,7 +43,8 @@ typedef enum tc_status {
     TC_ERR_CUDA = 4,          /* a CUDA runtime call failed */
     TC_ERR_TIMEOUT = 5,       /* a bounded device wait or retry loop gave up */
     TC_ERR_BUDGET = 6,        /* the request needs more device memory than the configured budget */
-    TC_ERR_UNSUPPORTED = 7    /* the input exceeds a limit of this build (e.g. n >= 2^31 - 1) */
+    TC_ERR_UNSUPPORTED = 7,   /* the input exceeds a limit of this build (e.g. n >= 2^31 - 1) */
+    TC_ERR_CANCELLED = 8      /* a queued serving request withdrawn by tc_server_cancel */
 } tc_status;
 
 /* Static text for a status code (never NULL). */
@@ -488,6 +489,14 @@ tc_status tc_server_create(int64_t hbm_budget_bytes, int32_t slots, int64_t grou
  */
 tc_status tc_server_submit(tc_server_t s, const int32_t* src, const int32_t* dst, int64_t m,
                            int32_t n, uint64_t tag);
+
+/*
+ * Withdraw the requests with this tag that are still waiting in the queue.  Their results
+ * come back from tc_server_poll with status TC_ERR_CANCELLED (and the server no longer
+ * borrows their arrays); requests already admitted to a slot run to the end.
+ *   n_cancelled  optional (host); receives how many requests were withdrawn.
+ */
+tc_status tc_server_cancel(tc_server_t s, uint64_t tag, int64_t* n_cancelled);
 
 /* Move up to max finished results into out (host, oldest first); *n_out: how many. */
 tc_status tc_server_poll(tc_server_t s, tc_result* out, int32_t max, int32_t* n_out);

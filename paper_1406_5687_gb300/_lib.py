@@ -17,9 +17,10 @@ _lock = threading.Lock()
 
 TC_OK = 0
 STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_VERTEX_RANGE", 3: "TC_ERR_OOM",
-                4: "TC_ERR_CUDA", 5: "TC_ERR_TIMEOUT", 6: "TC_ERR_BUDGET", 7: "TC_ERR_UNSUPPORTED"}
+                4: "TC_ERR_CUDA", 5: "TC_ERR_TIMEOUT", 6: "TC_ERR_BUDGET", 7: "TC_ERR_UNSUPPORTED",
+                8: "TC_ERR_CANCELLED"}
 (TC_ERR_INVALID_ARG, TC_ERR_VERTEX_RANGE, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_BUDGET,
- TC_ERR_UNSUPPORTED) = range(1, 8)
+ TC_ERR_UNSUPPORTED, TC_ERR_CANCELLED) = range(1, 9)
 TC_COST_EDGE, TC_COST_MERGE, TC_COST_ONE, TC_COST_DEGREE, TC_COST_PATRIC, TC_COST_NEW = range(6)
 TC_FN_ONE, TC_FN_DEGREE, TC_FN_PATRIC, TC_FN_NEW = range(4)
 TC_INPUT_SANITIZE, TC_INPUT_STRICT = 0, 1
@@ -139,6 +140,7 @@ SIGNATURES = {
                                         ctypes.POINTER(P)]),
     "tc_server_submit": (ctypes.c_int, [P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64]),
     "tc_server_poll": (ctypes.c_int, [P, ctypes.POINTER(Result), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "tc_server_cancel": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64)]),
     "tc_server_drain": (ctypes.c_int, [P, ctypes.c_int64]),
     "tc_server_get_stats": (ctypes.c_int, [P, ctypes.POINTER(ServerStats)]),
     "tc_server_destroy": (None, [P]),

@@ -109,11 +109,44 @@ class Batch:
             pass
 
 
-def autotune(graphs, options=None, reps: int = 3, stream=None, cap: int = 64):
+_TUNED_FIELDS = ("small_max", "warps_per_block", "big_warps", "piece", "static_percent")
+
+
+def workload_signature(graphs) -> str:
+    """Key of a tuning result: the device and log2 buckets of the workload's shape (graph
+    count, mean input edges, mean vertices)."""
+    import math
+    import torch
+    from . import _edge_ptrs
+    k = len(graphs)
+    m = [int(_edge_ptrs(s, d)[2]) for s, d, _ in graphs]
+    n = [int(nj) for _, _, nj in graphs]
+    b = lambda x: int(round(math.log2(max(x, 1))))  # noqa: E731
+    dev = torch.cuda.get_device_name(torch.cuda.current_device()) if torch.cuda.is_available() else "none"
+    return f"{dev}|k{b(k)}|m{b(sum(m) / max(k, 1))}|n{b(sum(n) / max(k, 1))}"
+
+
+def autotune(graphs, options=None, reps: int = 3, stream=None, cap: int = 64, cache_path=None):
     """Time the batched count of `graphs` over the library's grid of hub thresholds and
-    launch shapes.  Returns (best Options, report dict with every candidate's time)."""
-    from . import _stream, load
+    launch shapes.  Returns (best Options, report dict with every candidate's time).
+
+    With cache_path, a result tuned before for the same device and workload shape (see
+    workload_signature) is read from that JSON file instead, and new results are added."""
+    import json
+    import os
+    from . import _stream, default_options, load
     graphs = list(graphs)
+    sig = workload_signature(graphs) if cache_path else None
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+        if sig in cache:
+            base = options if options is not None else default_options()
+            best = _lib.Options()
+            ctypes.memmove(ctypes.byref(best), ctypes.byref(base), ctypes.sizeof(best))
+            for k in _TUNED_FIELDS:
+                setattr(best, k, int(cache[sig][k]))
+            return best, {"cached": True, "signature": sig, **cache[sig]}
     srcs, dsts, m, n, keep = _lists(graphs)
     best = _lib.Options()
     entries = (_lib.TuneEntry * cap)()
@@ -125,4 +158,17 @@ def autotune(graphs, options=None, reps: int = 3, stream=None, cap: int = 64):
     _lib.check(rc, "tc_batch_autotune")
     cands = [{"small_max": e.small_max, "warps_per_block": e.warps_per_block, "big_warps": e.big_warps,
               "piece": e.piece, "static_percent": e.static_percent, "ms": e.ms} for e in entries[:min(rep.n, cap)]]
-    return best, {"tried": rep.n, "best_ms": rep.best_ms, "default_ms": rep.default_ms, "candidates": cands}
+    report = {"cached": False, "tried": rep.n, "best_ms": rep.best_ms, "default_ms": rep.default_ms,
+              "candidates": cands}
+    if cache_path:
+        cache = {}
+        if os.path.exists(cache_path):
+            with open(cache_path) as f:
+                cache = json.load(f)
+        cache[sig] = {**{k: getattr(best, k) for k in _TUNED_FIELDS}, "best_ms": rep.best_ms}
+        tmp = f"{cache_path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
+        report["signature"] = sig
+    return best, report

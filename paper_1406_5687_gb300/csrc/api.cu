@@ -156,6 +156,7 @@ const char* tc_status_str(tc_status s) {
         case TC_ERR_TIMEOUT: return "bounded device wait gave up";
         case TC_ERR_BUDGET: return "device memory budget exceeded";
         case TC_ERR_UNSUPPORTED: return "input exceeds a limit of this build";
+        case TC_ERR_CANCELLED: return "request withdrawn before it ran";
     }
     return "unknown status";
 }

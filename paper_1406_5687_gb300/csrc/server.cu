@@ -226,6 +226,40 @@ tc_status tc_server_submit(tc_server_t sv, const int32_t* src, const int32_t* ds
     return TC_OK;
 }
 
+tc_status tc_server_cancel(tc_server_t sv, uint64_t tag, int64_t* n_cancelled) {
+    if (!sv) return TC_ERR_INVALID_ARG;
+    int64_t k = 0;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        const double t = now_s();
+        for (auto it = sv->queue.begin(); it != sv->queue.end();) {
+            if (it->tag != tag) {
+                ++it;
+                continue;
+            }
+            tc_result r;
+            std::memset(&r, 0, sizeof(r));
+            r.tag = it->tag;
+            r.status = TC_ERR_CANCELLED;
+            r.slot = -1;
+            r.group = 0;
+            r.t_submit = it->t_submit;
+            r.t_start = t;
+            r.t_done = t;
+            sv->results.push_back(r);
+            it = sv->queue.erase(it);
+            ++sv->finished;
+            ++k;
+        }
+    }
+    if (k) {
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_all();
+    }
+    if (n_cancelled) *n_cancelled = k;
+    return TC_OK;
+}
+
 tc_status tc_server_poll(tc_server_t sv, tc_result* out, int32_t max, int32_t* n_out) {
     if (!sv || !n_out || max < 0 || (max > 0 && !out)) return TC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(sv->mu);

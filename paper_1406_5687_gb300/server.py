@@ -41,6 +41,19 @@ class Server:
             _lib.check(rc, "tc_server_submit")
         return rid
 
+    def cancel(self, tag) -> int:
+        """Withdraw the still-queued requests submitted with `tag`; returns how many.  Their
+        results come back from poll with status TC_ERR_CANCELLED."""
+        from . import load
+        with self._lock:
+            rids = [rid for rid, (t, _) in self._pending.items() if t == tag]
+        n = 0
+        for rid in rids:
+            k = ctypes.c_int64()
+            _lib.check(load().tc_server_cancel(self._h, rid, ctypes.byref(k)), "tc_server_cancel")
+            n += k.value
+        return n
+
     def poll(self, max_results: int = 1024) -> list[dict]:
         from . import load
         buf = (_lib.Result * max(1, max_results))()

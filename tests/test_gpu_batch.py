@@ -175,3 +175,16 @@ def test_autotune_returns_a_candidate_that_counts_exactly(want):
     assert best.small_max in (32, 64, 128) and best.warps_per_block in (4, 8, 16)
     with tc.Batch.build(MIXED, options=best) as b:
         assert np.array_equal(b.count(), T)
+
+
+def test_autotune_cache_returns_the_stored_choice(tmp_path, want):
+    T, _ = want
+    path = str(tmp_path / "tune.json")
+    best, rep = tc.autotune(MIXED, reps=1, cache_path=path)
+    assert rep["cached"] is False and rep["signature"]
+    again, rep2 = tc.autotune(MIXED, reps=1, cache_path=path)
+    assert rep2["cached"] is True and rep2["signature"] == rep["signature"]
+    for k in ("small_max", "warps_per_block", "big_warps", "piece", "static_percent"):
+        assert getattr(again, k) == getattr(best, k)
+    with tc.Batch.build(MIXED, options=again) as b:
+        assert np.array_equal(b.count(), T)

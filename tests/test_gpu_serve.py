@@ -175,3 +175,23 @@ def test_destroy_with_requests_queued():
         s, d, n = POOL[0]
         sv.submit(s, d, n)
     sv.close()  # finishes what is in flight, drops the rest; must not hang
+
+
+def test_cancelled_requests_leave_the_others_unchanged(want):
+    """Requests withdrawn while queued come back as cancelled; every other result is exact."""
+    big = max(range(len(POOL)), key=lambda j: POOL[j][0].size)
+    with tc.Server(8 << 30, slots=1, group_edges=1) as sv:
+        sv.submit(*POOL[big][:2], POOL[big][2], tag="busy")  # occupies the only slot
+        for j in range(12):
+            sv.submit(*POOL[j][:2], POOL[j][2], tag=j)
+        withdrawn = sv.cancel(3) + sv.cancel(7) + sv.cancel("never submitted")
+        sv.drain(120_000)
+        res = {r["tag"]: r for r in sv.poll()}
+    assert len(res) == 13
+    cancelled = [j for j in (3, 7) if res[j]["status"] == _lib.TC_ERR_CANCELLED]
+    assert len(cancelled) == withdrawn  # a request already admitted runs to the end
+    for j in range(12):
+        if j in cancelled:
+            assert res[j]["total"] == 0 and res[j]["slot"] == -1
+        else:
+            assert res[j]["status"] == 0 and res[j]["total"] == int(want[j])
