@@ -69,6 +69,8 @@ def parse_args():
     p.add_argument("--serve-requests", type=int, default=0,
                    help="requests of the serving window (default: 256 as a leg of a single-graph run, 2000 "
                         "with --workload serve)")
+    p.add_argument("--serve-slots", type=int, default=4, help="slot threads of the server")
+    p.add_argument("--serve-group-edges", type=int, default=0, help="input edges one slot takes at once (0: default)")
     p.add_argument("--serve-pool", type=int, default=0,
                    help="pre-generated graphs the requests cycle through (default 32, or 256 with --workload serve)")
     p.add_argument("--batch-graphs", type=int, default=0,
@@ -454,7 +456,7 @@ def _pct(x, q):
     return float(np.percentile(np.asarray(x), q)) * 1e3
 
 
-def serve_leg(requests, pool_size, slots=4):
+def serve_leg(requests, pool_size, slots=4, group_edges=0):
     """The server (continuous batching, `slots` slot threads, 60 GB budget) against a
     one-at-a-time loop of tc_build + tc_count + tc_free, on the same Poisson arrival trace."""
     import numpy as np
@@ -468,7 +470,7 @@ def serve_leg(requests, pool_size, slots=4):
     pick = [i % pool_size for i in range(requests)]
     edges_in = sum(int(pool[j][0].numel()) for j in pick)
 
-    with tc.Server(SERVE_BUDGET, slots=slots) as sv:
+    with tc.Server(SERVE_BUDGET, slots=slots, group_edges=group_edges) as sv:
         for j in range(min(4, pool_size)):  # warm-up
             sv.submit(*pool[j], tag=-1)
         sv.drain(-1)
@@ -647,7 +649,7 @@ def run_serve_only(args, rank, world, local):
         "CUDA_VISIBLE_DEVICES") else str(local)
     clocks = ClockSampler(gpu_index)
     clocks.start()
-    leg = serve_leg(args.serve_requests or 2000, args.serve_pool or 256)
+    leg = serve_leg(args.serve_requests or 2000, args.serve_pool or 256, args.serve_slots, args.serve_group_edges)
     clk = clocks.stop()
     if rank == 0:
         sv = leg["served"]
@@ -923,7 +925,7 @@ def run_gpu(args, rank, world, local):
                           pack_edges=args.pack_edges)
     serve = None
     if rank == 0 and not args.no_serve:
-        serve = serve_leg(args.serve_requests or 256, args.serve_pool or 32)
+        serve = serve_leg(args.serve_requests or 256, args.serve_pool or 32, args.serve_slots, args.serve_group_edges)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
