@@ -6,6 +6,14 @@
  * (arXiv 1406.5687), Fig. 1, with the cost-balanced dynamic load balancing of
  * Sec. V (Eq. 1 and Eq. 2), run as CUDA kernels on one sm_103a GPU.
  *
+ * Steps of the path, as the comments below name them:
+ *   a1 canonical edge keys (ids checked, self-loops dropped)   a2 sort + dedupe
+ *   a3 degrees d_v          a4 orientation by the order of Sec. III-A
+ *   a5 the N+ lists of Fig. 1 (offsets, ascending lists)
+ *   a6 task costs, their prefix and the Eq. 1 / Eq. 2 schedule
+ *   a7 |N+(v) ∩ N+(u)| for every oriented edge (Fig. 1's last loop)
+ *   a8 the exact reduction to T (and optional T_v, per-edge counts)
+ *
  * Conventions for every call:
  *   - Vertex ids are int32 in [0, n).  Counts are exact uint64.
  *   - Pointers marked "host or device" may point to either; the library asks the

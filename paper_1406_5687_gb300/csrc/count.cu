@@ -13,8 +13,9 @@
 // at once, each in its own region of the warp's table.  Longer owners: a block stages a
 // window of consecutive owners into regions of one shared table and its warps pull
 // batches of 32 of the window's tasks from a block counter.
-// Inside a batch, partner lists of 32 or more entries are streamed by the whole warp one
-// list at a time; shorter ones are concatenated and spread over the lanes.
+// Inside a batch, the partner lists are read as one stream of 16-byte units spread over the
+// lanes (warp_batch_count); a big owner's partner lists are first trimmed to the part inside
+// the owner list's [first, last] range, the only part that can match.
 //
 // Schedule (Sec. V-B), per class.  The persistent grid has W workers, one per block (the
 // warps of a block share its chunk).  Task costs are prefix-summed (uint64).  The first
