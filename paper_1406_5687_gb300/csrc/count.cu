@@ -39,8 +39,8 @@ constexpr uint32_t kHashMul = 0x9E3779B1u;  // Knuth's multiplicative constant, 
 #ifndef TC_UNITS
 #define TC_UNITS 4
 #endif
-constexpr int kUnits = TC_UNITS;
-constexpr int kTvCacheLog = 11;  // 2048 (vertex, count) slots per block for per-vertex counts  // 16-byte units of partner lists a lane loads per step of warp_batch_count
+constexpr int kUnits = TC_UNITS;  // 16-byte units of partner lists a lane loads per step of warp_batch_count
+constexpr int kTvCacheLog = 11;   // 2048 (vertex, count) slots per block for per-vertex counts
 
 struct CountArgs {
     const int64_t* off;
