@@ -37,11 +37,13 @@ WORKLOAD_TEXT = {
     "ba": "barabasi-albert n=1,000,000 k=50 (avg degree 100), seed 1",
     "er": "erdos-renyi G(n=10,000, m=100,000), seed 0",
     "cl_small": "chung-lu n=2,000,000 exponent 2.1 mean degree 40 w0=44,721, 4.0e7 edge draws, seed 2 (profiling size)",
+    "cl_twitter": "chung-lu n=41,650,000 exponent 2.1 mean degree 115 w0=3e6, 2.4e9 edge draws, seed 5 "
+                  "(the size of the paper's Twitter graph)",
 }
 # input pairs of the same workload the oracle counts per CPU-baseline run (about 10-30 s)
-CPU_SAMPLE_PAIRS = {"cl": 32_000_000, "ba": 16_000_000, "er": 100_000, "cl_small": 8_000_000}
+CPU_SAMPLE_PAIRS = {"cl": 32_000_000, "ba": 16_000_000, "er": 100_000, "cl_small": 8_000_000, "cl_twitter": 32_000_000}
 # input pairs per step of the reference (oracle) arm, so that --steps K --warmup W ends in minutes
-REF_SAMPLE_PAIRS = {"cl": 4_000_000, "ba": 2_000_000, "er": 100_000, "cl_small": 2_000_000}
+REF_SAMPLE_PAIRS = {"cl": 4_000_000, "ba": 2_000_000, "er": 100_000, "cl_small": 2_000_000, "cl_twitter": 4_000_000}
 REF_BATCH_GRAPHS = 8
 REF_SERVE_GRAPHS = 2
 
@@ -51,7 +53,7 @@ def parse_args():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--workload", default="cl", choices=["cl", "ba", "er", "cl_small", "batch", "serve"])
+    p.add_argument("--workload", default="cl", choices=["cl", "ba", "er", "cl_small", "cl_twitter", "batch", "serve"])
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")

@@ -14,6 +14,8 @@ ba     Barabasi-Albert n=1,000,000, k=50 (avg degree 100), seed 1
 cl     Chung-Lu n=10,000,000, exponent 2.1, mean weight 40, w_0 = 1e5,
        2.0e8 edge draws (self-loops dropped and repeats merged by the counter's
        input policy), seed 2
+cl_twitter  the same recipe at Twitter's size (Table I): n=41,650,000,
+       mean weight 115, w_0 = 3e6, 2.4e9 edge draws, seed 5
 batch  4096 graphs, seed 3: even index Erdos-Renyi, odd index Barabasi-Albert;
        n log-uniform in [1e3, 2e5]; average degree uniform in [8, 128]
 serve  Poisson arrivals at 2,000 graphs/s of Chung-Lu graphs: exponent uniform
@@ -70,7 +72,11 @@ CL_10M = GraphSpec("cl", n=10_000_000, gamma=2.1, avg_deg=40.0, w_max=1e5, draws
 # profiling captures that must hold only a few GB on the device
 CL_2M = GraphSpec("cl", n=2_000_000, gamma=2.1, avg_deg=40.0, w_max=44721.0, draws=40_000_000, seed=2)
 
-SINGLE = {"er": ER_10K, "ba": BA_1M, "cl": CL_10M, "cl_small": CL_2M}
+# the Chung-Lu recipe at the size of the paper's largest real graph (Twitter, Table I: 42M
+# vertices, 2.4B edges): 41.65M vertices, 2.4e9 edge draws, mean weight 115, w_0 = 3e6
+CL_TWITTER = GraphSpec("cl", n=41_650_000, gamma=2.1, avg_deg=115.0, w_max=3e6, draws=2_400_000_000, seed=5)
+
+SINGLE = {"er": ER_10K, "ba": BA_1M, "cl": CL_10M, "cl_small": CL_2M, "cl_twitter": CL_TWITTER}
 
 
 def _unit(seed: int, tag: int, i: int) -> float:

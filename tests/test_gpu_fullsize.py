@@ -99,3 +99,41 @@ def test_serve_workload_sample():
         if specs[j].num_input_edges <= 4_000_000:
             want = oracle.count(oracle.oriented_csr(oracle.simple_graph(n, s.numpy(), d.numpy())), threads=THREADS)
             assert want == res[j]["total"], j
+
+
+@pytest.mark.slow
+def test_twitter_size_chung_lu():
+    """A Chung-Lu graph of the size of the paper's largest real graph (Twitter, Table I:
+    41.65M vertices, 2.4e9 edge draws), built and counted in device memory.  Too large for the
+    oracle's single-thread list build, so the checks are the method's own identities: the
+    cost-balanced parts sum to T, sum T_v = 3T, the per-edge counts sum to T, sampled per-edge
+    counts equal intersections of the built lists computed on the host, and the sampled lists
+    are ascending and oriented by the order of Sec. III-A."""
+    spec = W.SINGLE["cl_twitter"]
+    s, d = spec.edges()
+    sd, dd = torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda()
+    del s, d
+    with tc.Graph.build(sd, dd, spec.n) as g:
+        del sd, dd
+        info = g.info()
+        T = g.count()
+        assert sum(g.count_partition(p, 4) for p in range(4)) == T
+        T2, tv = g.count_per_vertex()
+        assert T2 == T and int(tv.sum().item()) == 3 * T
+        del tv
+        T3, pe = g.count_per_edge()
+        assert T3 == T and int(pe.sum().item()) == T
+        deg, off, cols, tasks = g.csr()
+        del tasks
+        off, cols, deg, pe = off.cpu().numpy(), cols.cpu().numpy(), deg.cpu().numpy(), pe.cpu().numpy()
+    assert int(off[-1]) == info["m_hat"]
+    rng = np.random.default_rng(11)
+    idx = rng.integers(0, info["m_hat"], 2000)
+    rows = np.searchsorted(off, idx, side="right") - 1
+    for i, v in zip(idx.tolist(), rows.tolist()):
+        u = int(cols[i])
+        assert (deg[v], v) < (deg[u], u)
+        a, b = cols[off[v]:off[v + 1]], cols[off[u]:off[u + 1]]
+        assert int(pe[i]) == len(np.intersect1d(a, b, assume_unique=True)), (v, u)
+    for v in rng.integers(0, spec.n, 20000).tolist():
+        assert np.all(np.diff(cols[off[v]:off[v + 1]]) > 0)
