@@ -449,3 +449,25 @@ def test_partition_arguments():
             with pytest.raises(tc.TcError) as e:
                 g.count_partition(part, nparts)
             assert e.value.code == tc._lib.TC_ERR_INVALID_ARG
+
+
+def test_largest_vertex_count():
+    """n = 2^30, the largest supported: K_5 on the five highest ids and a wheel W_100 on the
+    lowest, so T = C(5,3) + 99 by the closed forms, with per-vertex counts at both ends."""
+    n = 1 << 30
+    top = np.arange(n - 5, n, dtype=np.int64)
+    iu = np.triu_indices(5, 1)
+    s1, d1 = top[iu[0]], top[iu[1]]
+    wn, ws, wd = F.wheel(100)
+    s = np.concatenate([s1, ws.astype(np.int64)]).astype(np.int32)
+    d = np.concatenate([d1, wd.astype(np.int64)]).astype(np.int32)
+    with tc.Graph.build(s, d, n) as g:
+        assert g.count() == 10 + 99
+        T, tv = g.count_per_vertex()
+        assert T == 109
+        assert tv[n - 5:].tolist() == [6] * 5          # each K_5 vertex is in C(4,2) triangles
+        assert int(tv[:100].sum().item()) == 3 * 99
+        assert sum(g.count_partition(p, 3) for p in range(3)) == 109
+    with pytest.raises(tc.TcError) as e:
+        tc.Graph.build(s, d, n + 1)
+    assert e.value.code == tc._lib.TC_ERR_UNSUPPORTED
