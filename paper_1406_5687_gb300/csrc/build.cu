@@ -170,14 +170,26 @@ __global__ void k_orient(const uint64_t* __restrict__ ukeys, int64_t mh, int b, 
 }
 
 // --------------------------------------------------------------------------- a5: N+ lists
-__global__ void k_dhat_count(const uint64_t* __restrict__ okeys, int64_t mh, int b, int32_t* __restrict__ dhat) {
+// One pass over the oriented keys, sorted by owner: the lists are the keys' low bits in this
+// order (cols[i] is the partner of key i), and d_hat counts each owner's run of keys (the
+// first lane of each run within a warp adds the run's length).
+__global__ void k_lists(const uint64_t* __restrict__ okeys, int64_t mh, int b, int32_t* __restrict__ dhat,
+                        int32_t* __restrict__ cols) {
+    const uint64_t mask = (1ull << b) - 1;
     const int lane = threadIdx.x & 31;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i - lane < mh;
          i += (int64_t)gridDim.x * blockDim.x) {
-        bool in = i < mh;
-        uint32_t v = in ? (uint32_t)(okeys[i] >> b) : 0xFFFFFFFFu;
-        unsigned peers = __match_any_sync(kFull, v);
-        if (in && lane == __ffs(peers) - 1) atomicAdd(&dhat[v], __popc(peers));
+        const bool in = i < mh;
+        const uint64_t k = in ? okeys[i] : 0ull;
+        const uint32_t v = in ? (uint32_t)(k >> b) : 0xFFFFFFFFu;
+        if (in) cols[i] = (int32_t)(k & mask);
+        const uint32_t prev = __shfl_up_sync(kFull, v, 1);
+        const bool head = in && (lane == 0 || v != prev);
+        const unsigned heads = __ballot_sync(kFull, head);
+        const int n_in = __popc(__ballot_sync(kFull, in));  // valid lanes are 0 .. n_in - 1
+        const unsigned after = heads & ~lanemask_le();
+        const int run_end = after ? __ffs(after) - 1 : n_in;
+        if (head) atomicAdd(&dhat[v], run_end - lane);
     }
 }
 
@@ -185,12 +197,6 @@ struct DhatVal {
     const int32_t* d;
     __device__ uint64_t operator()(int64_t i) const { return (uint64_t)d[i]; }
 };
-
-__global__ void k_cols(const uint64_t* __restrict__ okeys, int64_t mh, int b, int32_t* __restrict__ cols) {
-    const uint64_t mask = (1ull << b) - 1;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mh; i += (int64_t)gridDim.x * blockDim.x)
-        cols[i] = (int32_t)(okeys[i] & mask);
-}
 
 __global__ void k_max_deg(const int32_t* __restrict__ deg, const int32_t* __restrict__ dhat, int32_t n,
                           BuildCounters* cnt) {
@@ -398,23 +404,19 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     TC_TRY(check_device_error(g, s));
     uint64_t* free_buf = osorted == spare ? ukeys : spare;
     // a5
-    if (mh > 0) {
-        k_dhat_count<<<grid_stride_blocks(mh), kThreads, 0, s>>>(osorted, mh, b, dhat.ptr);
-        note_launch();
-    }
     DevBuf<int64_t> off;
     DevBuf<int32_t> cols;
     TC_TRY(off.alloc(al, (size_t)n + 1, s));
     TC_TRY(cols.alloc(al, (size_t)(mh > 0 ? mh : 1) + 4, s));  // +4: 16-byte vector reads may run past the end
+    if (mh > 0) {
+        k_lists<<<grid_stride_blocks(mh), kThreads, 0, s>>>(osorted, mh, b, dhat.ptr, cols.ptr);
+        note_launch();
+    }
     {
         // offsets = exclusive scan of dhat (values < 2^63, so the uint64 scan is the int64 array)
         DevBuf<uint64_t> scr;
         TC_TRY(scr.alloc(al, scan_scratch_words(n), s));
         TC_CUDA_TRY(scan_exclusive(DhatVal{dhat.ptr}, n, reinterpret_cast<uint64_t*>(off.ptr), scr.ptr, s));
-    }
-    if (mh > 0) {
-        k_cols<<<grid_stride_blocks(mh), kThreads, 0, s>>>(osorted, mh, b, cols.ptr);
-        note_launch();
     }
     if (n > 0) {
         k_max_deg<<<grid_stride_blocks(n), kThreads, 0, s>>>(deg.ptr, dhat.ptr, n, cnt.ptr);
