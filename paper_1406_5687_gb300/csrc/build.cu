@@ -106,7 +106,9 @@ tc_status compact(Pred p, Val v, int64_t n, OutT* out, Allocator* al, cudaStream
 
 // --------------------------------------------------------------------------- a1: canonical keys
 __global__ void k_canon(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m, int32_t n,
-                        int b, uint64_t sent, uint64_t* __restrict__ keys, BuildCounters* cnt) {
+                        int b, uint64_t sent, uint64_t* __restrict__ keys, BuildCounters* cnt, DigitCounts dc) {
+    extern __shared__ unsigned dc_sh[];
+    digit_counts_init(dc, dc_sh);
     const int lane = threadIdx.x & 31;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i - lane < m;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -116,12 +118,15 @@ __global__ void k_canon(const int32_t* __restrict__ src, const int32_t* __restri
         bool loop = in && !bad && a == c;
         if (in) {
             uint64_t lo = (uint64_t)(uint32_t)(a < c ? a : c), hi = (uint64_t)(uint32_t)(a < c ? c : a);
-            keys[i] = (bad || loop) ? sent : ((lo << b) | hi);
+            const uint64_t k = (bad || loop) ? sent : ((lo << b) | hi);
+            keys[i] = k;
+            digit_counts_add(dc, dc_sh, k);
         }
         if (bad) atomicMin(&cnt->bad_index, (long long)i);
         unsigned lb = __ballot_sync(kFull, loop);
         if (lane == 0 && lb) atomicAdd(&cnt->self_loops, (unsigned long long)__popc(lb));
     }
+    digit_counts_flush(dc, dc_sh);
 }
 
 struct UniquePred {
@@ -158,15 +163,20 @@ __global__ void k_degree(const uint64_t* __restrict__ ukeys, int64_t mh, int b, 
 
 // --------------------------------------------------------------------------- a4: orientation
 __global__ void k_orient(const uint64_t* __restrict__ ukeys, int64_t mh, int b, const int32_t* __restrict__ deg,
-                         uint64_t* __restrict__ okeys) {
+                         uint64_t* __restrict__ okeys, DigitCounts dc) {
+    extern __shared__ unsigned dc_sh[];
+    digit_counts_init(dc, dc_sh);
     const uint64_t mask = (1ull << b) - 1;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mh; i += (int64_t)gridDim.x * blockDim.x) {
         uint64_t k = ukeys[i];
         uint32_t a = (uint32_t)(k >> b), c = (uint32_t)(k & mask);  // a < c
-        int32_t da = deg[a], dc = deg[c];
-        bool a_first = da < dc || (da == dc);  // equal degrees: the smaller id a comes first
-        okeys[i] = a_first ? k : (((uint64_t)c << b) | a);
+        int32_t da = deg[a], dcd = deg[c];
+        bool a_first = da < dcd || (da == dcd);  // equal degrees: the smaller id a comes first
+        const uint64_t o = a_first ? k : (((uint64_t)c << b) | a);
+        okeys[i] = o;
+        digit_counts_add(dc, dc_sh, o);
     }
+    digit_counts_flush(dc, dc_sh);
 }
 
 // --------------------------------------------------------------------------- a5: N+ lists
@@ -240,7 +250,9 @@ __global__ void k_renumber(const int32_t* __restrict__ dhat, int small_max, cons
 // number alone keeps each owner's tasks in the order of their oriented edges in the lists.
 __global__ void k_task_keys(const uint64_t* __restrict__ okeys, const int32_t* __restrict__ cols, int64_t mh, int b,
                             const int32_t* __restrict__ dhat, int small_max, const uint32_t* __restrict__ rid,
-                            int32_t n, uint64_t* __restrict__ tkeys, BuildCounters* cnt) {
+                            int32_t n, uint64_t* __restrict__ tkeys, BuildCounters* cnt, DigitCounts dcn) {
+    extern __shared__ unsigned dc_sh[];
+    digit_counts_init(dcn, dc_sh);
     const int lane = threadIdx.x & 31;
     unsigned long long sv = 0, su = 0, ss = 0, nt = 0, nsm = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mh; i += (int64_t)gridDim.x * blockDim.x) {
@@ -260,8 +272,11 @@ __global__ void k_task_keys(const uint64_t* __restrict__ okeys, const int32_t* _
             nsm += big ? 0ull : 1ull;
             num = rid[o];
         }
-        tkeys[i] = (num << 32) | p;
+        const uint64_t key = (num << 32) | p;
+        tkeys[i] = key;
+        digit_counts_add(dcn, dc_sh, key);
     }
+    digit_counts_flush(dcn, dc_sh);
     sv = warp_sum(sv);
     su = warp_sum(su);
     ss = warp_sum(ss);
@@ -313,9 +328,25 @@ static int bits_for(int32_t n) {
     return b < 1 ? 1 : b;
 }
 
+constexpr int kMaxSortPasses = 8;  // 64-bit keys
+static int sort_passes(int nbits) { return (nbits + 7) / 8; }
+
+static tc_status zero_counts(const DigitCounts& dc, cudaStream_t s) {
+    TC_CUDA_TRY(cudaMemsetAsync(dc.global, 0, sizeof(unsigned long long) * dc.npass * 256, s));
+    return TC_OK;
+}
+
 static unsigned grid_stride_blocks(int64_t n) {
     int64_t want = ceil_div(n > 0 ? n : 1, kThreads);
     int64_t cap = (int64_t)num_sms() * 16;
+    return (unsigned)(want < cap ? want : cap);
+}
+
+// Grid of a kernel that also counts its keys' digits: one wave of fully resident blocks, so
+// that few blocks add their shared counts to the global ones.
+static unsigned count_blocks(int64_t n) {
+    int64_t want = ceil_div(n > 0 ? n : 1, kThreads);
+    int64_t cap = (int64_t)num_sms() * (2048 / kThreads);
     return (unsigned)(want < cap ? want : cap);
 }
 
@@ -349,15 +380,23 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     TC_TRY(ka.alloc(al, m > 0 ? m : 1, s));
     TC_TRY(kb.alloc(al, m > 0 ? m : 1, s));
 
+    // digit counts of each sort's keys, gathered by the kernel that writes them
+    DevBuf<unsigned long long> counts;
+    TC_TRY(counts.alloc(al, (size_t)kMaxSortPasses * 256, s));
+
     // a1
+    unsigned long long* const ucounts = counts.ptr;
     if (m > 0) {
-        k_canon<<<grid_stride_blocks(m), kThreads, 0, s>>>(src, dst, m, n, b, sent, ka.ptr, cnt.ptr);
+        const DigitCounts dc{ucounts, 0, sort_passes(nbits)};
+        TC_TRY(zero_counts(dc, s));
+        k_canon<<<count_blocks(m), kThreads, digit_counts_bytes(dc), s>>>(src, dst, m, n, b, sent, ka.ptr, cnt.ptr,
+                                                                          dc);
         note_launch();
     }
     TC_CUDA_TRY(cudaGetLastError());
     // a2
     uint64_t* sorted = nullptr;
-    TC_TRY(radix_sort_u64(ka.ptr, kb.ptr, m, 0, nbits, al, s, &sorted, g->status, spin));
+    TC_TRY(radix_sort_u64(ka.ptr, kb.ptr, m, 0, nbits, al, s, &sorted, g->status, spin, m > 0 ? ucounts : nullptr));
     TC_TRY(check_device_error(g, s));
     uint64_t* other = sorted == ka.ptr ? kb.ptr : ka.ptr;
     uint64_t mh64 = 0;
@@ -391,7 +430,9 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     }
     // a4
     if (mh > 0) {
-        k_orient<<<grid_stride_blocks(mh), kThreads, 0, s>>>(ukeys, mh, b, deg.ptr, spare);
+        const DigitCounts dc{ucounts, b, sort_passes(b)};
+        TC_TRY(zero_counts(dc, s));
+        k_orient<<<count_blocks(mh), kThreads, digit_counts_bytes(dc), s>>>(ukeys, mh, b, deg.ptr, spare, dc);
         note_launch();
     }
     TC_CUDA_TRY(cudaGetLastError());
@@ -400,7 +441,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     // partners below v come from earlier runs (keys (u, v), u ascending), its partners above v
     // from v's own run (keys (v, x), x ascending), in that order.
     uint64_t* osorted = nullptr;
-    TC_TRY(radix_sort_u64(spare, ukeys, mh, b, b, al, s, &osorted, g->status, spin));
+    TC_TRY(radix_sort_u64(spare, ukeys, mh, b, b, al, s, &osorted, g->status, spin, mh > 0 ? ucounts : nullptr));
     TC_TRY(check_device_error(g, s));
     uint64_t* free_buf = osorted == spare ? ukeys : spare;
     // a5
@@ -436,14 +477,18 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         k_renumber<<<grid_stride_blocks(n), kThreads, 0, s>>>(dhat.ptr, g->opt.small_max, bex.ptr, n, rid.ptr, inv.ptr);
         note_launch();
     }
+    const int task_bits = bits_for(n + 1);
     if (mh > 0) {
-        k_task_keys<<<grid_stride_blocks(mh), kThreads, 0, s>>>(osorted, cols.ptr, mh, b, dhat.ptr,
-                                                                g->opt.small_max, rid.ptr, n, free_buf, cnt.ptr);
+        const DigitCounts dc{ucounts, 32, sort_passes(task_bits)};
+        TC_TRY(zero_counts(dc, s));
+        k_task_keys<<<count_blocks(mh), kThreads, digit_counts_bytes(dc), s>>>(
+            osorted, cols.ptr, mh, b, dhat.ptr, g->opt.small_max, rid.ptr, n, free_buf, cnt.ptr, dc);
         note_launch();
     }
     TC_CUDA_TRY(cudaGetLastError());
     uint64_t* tsorted = nullptr;
-    TC_TRY(radix_sort_u64(free_buf, osorted, mh, 32, bits_for(n + 1), al, s, &tsorted, g->status, spin));
+    TC_TRY(radix_sort_u64(free_buf, osorted, mh, 32, task_bits, al, s, &tsorted, g->status, spin,
+                          mh > 0 ? ucounts : nullptr));
     TC_TRY(check_device_error(g, s));
     TC_CUDA_TRY(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(hc), cudaMemcpyDeviceToHost, s));
     TC_CUDA_TRY(cudaStreamSynchronize(s));

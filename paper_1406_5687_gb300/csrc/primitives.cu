@@ -300,7 +300,8 @@ int64_t radix_sort_scratch_bytes(int64_t n) {
 }
 
 tc_status radix_sort_u64(uint64_t* keys, uint64_t* tmp, int64_t n, int lo_bit, int nbits, Allocator* al,
-                         cudaStream_t s, uint64_t** result, DevStatus* err, long long spin_limit) {
+                         cudaStream_t s, uint64_t** result, DevStatus* err, long long spin_limit,
+                         unsigned long long* counts) {
     *result = keys;
     if (n <= 1 || nbits <= 0) return TC_OK;
     if (lo_bit < 0 || lo_bit + nbits > 64) return TC_ERR_INVALID_ARG;
@@ -308,26 +309,32 @@ tc_status radix_sort_u64(uint64_t* keys, uint64_t* tmp, int64_t n, int lo_bit, i
     const int64_t ntiles = ceil_div(n, kOsTile);
     if (ntiles > 0xFFFFFFFFll) return TC_ERR_UNSUPPORTED;
     TC_CUDA_TRY(cudaFuncSetAttribute(k_os_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOsSmem));
-    DevBuf<unsigned long long> ghist, status;
+    DevBuf<unsigned long long> own_hist, status;
     DevBuf<unsigned> counters;
-    TC_TRY(ghist.alloc(al, (size_t)npass * kRadix, s));
+    unsigned long long* ghist = counts;
+    if (!counts) {
+        TC_TRY(own_hist.alloc(al, (size_t)npass * kRadix, s));
+        ghist = own_hist.ptr;
+    }
     TC_TRY(status.alloc(al, (size_t)ntiles * kRadix, s));
     TC_TRY(counters.alloc(al, (size_t)npass, s));
-    TC_CUDA_TRY(cudaMemsetAsync(ghist.ptr, 0, sizeof(unsigned long long) * npass * kRadix, s));
     TC_CUDA_TRY(cudaMemsetAsync(counters.ptr, 0, sizeof(unsigned) * npass, s));
-    const int64_t hblocks = ntiles < (int64_t)num_sms() * 8 ? ntiles : (int64_t)num_sms() * 8;
-    const size_t hsmem = (size_t)kOsWarps * npass * kRadix * sizeof(unsigned);
-    TC_CUDA_TRY(cudaFuncSetAttribute(k_os_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
-    k_os_hist<<<(unsigned)hblocks, kOsBlock, hsmem, s>>>(keys, n, lo_bit, npass, ghist.ptr);
-    note_launch();
-    k_os_bases<<<npass, kRadix, 0, s>>>(ghist.ptr);
+    if (!counts) {
+        TC_CUDA_TRY(cudaMemsetAsync(ghist, 0, sizeof(unsigned long long) * npass * kRadix, s));
+        const int64_t hblocks = ntiles < (int64_t)num_sms() * 8 ? ntiles : (int64_t)num_sms() * 8;
+        const size_t hsmem = (size_t)kOsWarps * npass * kRadix * sizeof(unsigned);
+        TC_CUDA_TRY(cudaFuncSetAttribute(k_os_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
+        k_os_hist<<<(unsigned)hblocks, kOsBlock, hsmem, s>>>(keys, n, lo_bit, npass, ghist);
+        note_launch();
+    }
+    k_os_bases<<<npass, kRadix, 0, s>>>(ghist);
     note_launch();
     TC_CUDA_TRY(cudaGetLastError());
     uint64_t* a = keys;
     uint64_t* b = tmp;
     for (int p = 0; p < npass; ++p) {
         TC_CUDA_TRY(cudaMemsetAsync(status.ptr, 0, sizeof(unsigned long long) * ntiles * kRadix, s));
-        k_os_pass<<<(unsigned)ntiles, kOsBlock, kOsSmem, s>>>(a, b, n, lo_bit + 8 * p, ghist.ptr + (int64_t)p * kRadix,
+        k_os_pass<<<(unsigned)ntiles, kOsBlock, kOsSmem, s>>>(a, b, n, lo_bit + 8 * p, ghist + (int64_t)p * kRadix,
                                                                status.ptr, counters.ptr + p, err, spin_limit);
         note_launch();
         TC_CUDA_TRY(cudaGetLastError());

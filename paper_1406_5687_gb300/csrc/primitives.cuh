@@ -10,8 +10,40 @@ namespace tcg {
 // keys / tmp holds the sorted sequence.  Scratch for the digit counts comes from `al`.
 // A look-back wait that exceeds spin_limit iterations sets TC_ERR_TIMEOUT in *err (the
 // caller must check it before using the result).
+// counts: optional (device, ceil(nbits / 8) * 256 uint64): the digit counts of the keys,
+// gathered by the kernel that wrote them (DigitCounts below); the sort then skips its own
+// counting pass and uses the array as scratch.
 tc_status radix_sort_u64(uint64_t* keys, uint64_t* tmp, int64_t n, int lo_bit, int nbits, Allocator* al,
-                         cudaStream_t s, uint64_t** result, DevStatus* err, long long spin_limit);
+                         cudaStream_t s, uint64_t** result, DevStatus* err, long long spin_limit,
+                         unsigned long long* counts = nullptr);
+
+// Digit counts of the keys a kernel writes, for radix_sort_u64 over bits
+// [lo_bit, lo_bit + 8 npass): the block counts into npass * 256 shared counters (dynamic
+// shared memory of digit_counts_bytes) and adds them to `global` (zeroed by the caller) at
+// its end.  Every thread of the block calls init and flush.
+struct DigitCounts {
+    unsigned long long* global;
+    int lo_bit;
+    int npass;
+};
+
+inline size_t digit_counts_bytes(const DigitCounts& dc) { return (size_t)dc.npass * 256 * sizeof(unsigned); }
+
+__device__ __forceinline__ void digit_counts_init(const DigitCounts& dc, unsigned* sh) {
+    for (int i = threadIdx.x; i < dc.npass * 256; i += blockDim.x) sh[i] = 0u;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void digit_counts_add(const DigitCounts& dc, unsigned* sh, uint64_t key) {
+    const uint64_t k = key >> dc.lo_bit;
+    for (int p = 0; p < dc.npass; ++p) atomicAdd(&sh[p * 256 + (unsigned)((k >> (8 * p)) & 0xFF)], 1u);
+}
+
+__device__ __forceinline__ void digit_counts_flush(const DigitCounts& dc, const unsigned* sh) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < dc.npass * 256; i += blockDim.x)
+        if (sh[i]) atomicAdd(&dc.global[i], (unsigned long long)sh[i]);
+}
 
 // Bytes of scratch radix_sort_u64 takes from the allocator for n keys (for budgets).
 int64_t radix_sort_scratch_bytes(int64_t n);
