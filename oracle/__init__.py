@@ -66,6 +66,8 @@ def _load():
             L.or_oriented_csr.restype = ctypes.c_int
             L.or_count.argtypes = [i32, P, P, P, P, ctypes.c_int]
             L.or_count.restype = u64
+            L.or_count_parts.argtypes = [i32, P, P, i32, P, P]
+            L.or_count_parts.restype = ctypes.c_int
             L.or_vertex_cost.argtypes = [ctypes.c_int, i32, P, P, P, P]
             L.or_vertex_cost.restype = ctypes.c_int
             L.or_tasks.argtypes = [i32, P, P, i64, P, P, P, ctypes.POINTER(i64)]
@@ -151,6 +153,20 @@ def count(csr: OrientedCSR, per_edge=False, per_vertex=False, threads=1):
     if not per_edge and not per_vertex:
         return T
     return T, (pe[:csr.m_hat] if per_edge else None), (tv[:csr.n] if per_vertex else None)
+
+
+def count_parts(csr: OrientedCSR, cuts) -> np.ndarray:
+    """Sec. IV-A / IV-C: the P x P table of SurrogateCount sums over the non-overlapping
+    partition with vertex sets [cuts[j], cuts[j+1]): entry (i, j) is what processor j counts
+    for the lists N_v, v in V_i, that it receives.  The table sums to T."""
+    L = _load()
+    cuts = np.ascontiguousarray(cuts, dtype=np.int32)
+    P = len(cuts) - 1
+    out = np.zeros(max(P, 1) * max(P, 1), np.uint64)
+    rc = L.or_count_parts(csr.n, _p(csr.off), _p(csr.cols), P, _p(cuts), _p(out))
+    if rc != OK:
+        raise OracleError(rc, "bad cuts")
+    return out[:P * P].reshape(P, P)
 
 
 def count_edges(n, src, dst, strict=False, threads=1) -> int:

@@ -30,6 +30,13 @@
  *                     PATRIC estimate sum_{u in N_v}(dh_v + dh_u) (Sec. IV-B) and
  *                     the new estimate sum_{u in Nfull_v - N_v}(dh_v + dh_u)
  *                     (Sec. IV-F), dh = effective degree |N_v|.
+ *   or_count_parts    Sec. IV-A and IV-C: V split into P sets of consecutive
+ *                     vertices (Def. 1); processor i sends N_v (v in V_i) once
+ *                     to every processor j that owns some u in N_v (the
+ *                     surrogate approach, with its LastProc variable), and j
+ *                     adds SurrogateCount(N_v, j) = sum over u in N_v with u in
+ *                     V_j of |N_u intersect N_v|.  The result is the P x P table
+ *                     of those sums by (sender i, counter j), whose total is T.
  *   or_tasks,         The GPU's work decomposition, restated from its
  *   or_task_costs,    definition: each oriented edge becomes one task owned by
  *   or_schedule       the endpoint with the longer list, in a small or a big
@@ -211,6 +218,55 @@ uint64_t or_count(int32_t n, const int64_t* off, const int32_t* cols, uint32_t* 
         }
     }
     return T;
+}
+
+/* The processor (part) that holds vertex u: cuts[j] <= u < cuts[j + 1]. */
+static int32_t part_of(int32_t u, int32_t nparts, const int32_t* cuts) {
+    int32_t j = 0;
+    while (j + 1 < nparts && u >= cuts[j + 1]) ++j;
+    return j;
+}
+
+/* SurrogateCount (Sec. IV-C): processor j receives X = N_v and, for every u in X that it
+ * owns, counts |N_u intersect X|. */
+static uint64_t surrogate_count(const int32_t* X, int64_t nx, int32_t j, int32_t nparts, const int32_t* cuts,
+                                const int64_t* off, const int32_t* cols) {
+    uint64_t T = 0;
+    for (int64_t k = 0; k < nx; ++k) {
+        const int32_t u = X[k];
+        if (part_of(u, nparts, cuts) != j) continue;
+        T += merge_count(cols + off[u], off[u + 1] - off[u], X, nx, u, u, NULL);
+    }
+    return T;
+}
+
+/*
+ * Sec. IV-A and IV-C: the count over a non-overlapping partition (Def. 1) of the vertices
+ * into nparts sets of consecutive vertices, V_j = [cuts[j], cuts[j+1]) (cuts[0] = 0,
+ * cuts[nparts] = n, non-decreasing; empty sets allowed).  For every v in V_i, N_v is sent
+ * to processor j when a u in N_v with u in V_j is met and j differs from the last processor
+ * N_v went to (LastProc; N_v is sorted and the V_j are consecutive, so that is once per
+ * j); j adds SurrogateCount(N_v, j) to out[i * nparts + j] (zeroed here).
+ */
+int or_count_parts(int32_t n, const int64_t* off, const int32_t* cols, int32_t nparts, const int32_t* cuts,
+                   uint64_t* out) {
+    if (n < 0 || nparts < 1 || cuts[0] != 0 || cuts[nparts] != n) return OR_ERR_INVALID_ARG;
+    for (int32_t j = 0; j < nparts; ++j)
+        if (cuts[j] > cuts[j + 1]) return OR_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(uint64_t) * (size_t)nparts * (size_t)nparts);
+    for (int32_t i = 0; i < nparts; ++i) {
+        for (int32_t v = cuts[i]; v < cuts[i + 1]; ++v) {
+            int32_t last_proc = -1;
+            for (int64_t k = off[v]; k < off[v + 1]; ++k) {
+                const int32_t j = part_of(cols[k], nparts, cuts);
+                if (j == last_proc) continue;
+                out[(size_t)i * nparts + j] +=
+                    surrogate_count(cols + off[v], off[v + 1] - off[v], j, nparts, cuts, off, cols);
+                last_proc = j;
+            }
+        }
+    }
+    return OR_OK;
 }
 
 enum { OR_COST_ONE = 0, OR_COST_DEGREE = 1, OR_COST_PATRIC = 2, OR_COST_NEW = 3 };

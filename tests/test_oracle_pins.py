@@ -283,3 +283,54 @@ def test_er_config0_expected_count():
     # variance of a triangle count in G(n,p): the triangle term plus pairs sharing an edge
     var = mean * (1 - p ** 3) + math.comb(n, 4) * 6 * p ** 5 * (1 - p)
     assert abs(T - mean) < 6 * math.sqrt(var)
+
+
+# --------------------------------------------------------------------------- partitioned count
+
+def _random_cuts(rng, n, P):
+    inner = np.sort(rng.integers(0, n + 1, P - 1))
+    return np.array([0, *inner, n], np.int64)
+
+
+@pytest.mark.parametrize("seed", [10, 11, 12])
+def test_partition_table_by_brute_force(seed):
+    """Sec. IV-A / IV-C: the triangle x1 < x2 < x3 (degree order) is found once, on the
+    oriented edge (x1, x2): by the processor holding x2, in the list N_x1 sent by the
+    processor holding x1.  Degrees and parts come from the adjacency matrix here."""
+    n, s, d = _some_graph(seed)
+    csr = oracle.oriented_csr(oracle.simple_graph(n, s, d))
+    deg = BF.adjacency(n, s, d).sum(1)
+    tris = BF.triangle_list(n, s, d)
+    rng = np.random.default_rng(seed)
+    for P in (1, 2, 3, 5, 8, 40):
+        cuts = _random_cuts(rng, n, P)
+        part = np.searchsorted(cuts, np.arange(n), side="right") - 1
+        expect = np.zeros((P, P), np.int64)
+        for tri in tris:
+            x1, x2, _ = sorted(tri, key=lambda x: (int(deg[x]), x))
+            expect[part[x1], part[x2]] += 1
+        got = oracle.count_parts(csr, cuts).astype(np.int64)
+        assert np.array_equal(got, expect), (P, cuts)
+
+
+def test_partition_table_sums_to_T_and_empty_parts():
+    import graphgen
+    n = 3000
+    s, d = graphgen.chung_lu(n, 2.05, 20.0, 600.0, 40_000, 5)
+    csr = oracle.oriented_csr(oracle.simple_graph(n, s, d))
+    T = oracle.count(csr)
+    assert oracle.count_parts(csr, [0, n]).tolist() == [[T]]
+    # empty sets of vertices anywhere, including first and last
+    for cuts in ([0, 0, 100, 100, 2999, n, n], [0, 1, 2, 3, n], [0, n, n]):
+        tab = oracle.count_parts(csr, cuts)
+        assert int(tab.sum()) == T
+        sizes = np.diff(cuts)
+        assert np.all(tab[sizes == 0, :] == 0) and np.all(tab[:, sizes == 0] == 0)
+
+
+def test_partition_bad_cuts():
+    n, s, d = _some_graph(13)
+    csr = oracle.oriented_csr(oracle.simple_graph(n, s, d))
+    for cuts in ([1, n], [0, n - 1], [0, 300, 200, n]):
+        with pytest.raises(oracle.OracleError):
+            oracle.count_parts(csr, cuts)
