@@ -182,7 +182,7 @@ tc_status tc_count_async(tc_graph_t g, tc_stream_t stream, uint64_t* total_dev);
  * exclusive cost prefix lies in [C p / P, C (p + 1) / P) -- Sec. IV-B's cost-balanced
  * partition, applied to the task costs of a6 -- and schedules them by Eq. 1 + Eq. 2 among
  * this GPU's workers.  Every task lies in exactly one part, so the sum of the P partial
- * counts (one uint64 reduction, the MPI_Reduce of Fig. 5) is T.
+ * counts (one uint64 reduction, the MPI_Reduce of Fig. 11) is T.
  *   part, nparts  0 <= part < nparts.
  *   partial       host; receives this part's count.
  * Synchronises `stream`.
