@@ -68,6 +68,8 @@ def _load():
             L.or_count.restype = u64
             L.or_count_parts.argtypes = [i32, P, P, i32, P, P]
             L.or_count_parts.restype = ctypes.c_int
+            L.or_balanced_cuts.argtypes = [i32, P, i32, P]
+            L.or_balanced_cuts.restype = ctypes.c_int
             L.or_vertex_cost.argtypes = [ctypes.c_int, i32, P, P, P, P]
             L.or_vertex_cost.restype = ctypes.c_int
             L.or_tasks.argtypes = [i32, P, P, i64, P, P, P, ctypes.POINTER(i64)]
@@ -167,6 +169,18 @@ def count_parts(csr: OrientedCSR, cuts) -> np.ndarray:
     if rc != OK:
         raise OracleError(rc, "bad cuts")
     return out[:P * P].reshape(P, P)
+
+
+def balanced_cuts(f, P: int) -> np.ndarray:
+    """Sec. IV-A: cuts (P + 1 int32) of V into P sets of consecutive vertices of about equal cost:
+    cut k is the first q whose cost prefix f(0) + ... + f(q-1) reaches k/P of the total."""
+    L = _load()
+    f = np.ascontiguousarray(f, dtype=np.uint64)
+    cuts = np.zeros(int(P) + 1, np.int32)
+    rc = L.or_balanced_cuts(len(f), _p(f), int(P), _p(cuts))
+    if rc != OK:
+        raise OracleError(rc, "bad part count")
+    return cuts
 
 
 def count_edges(n, src, dst, strict=False, threads=1) -> int:

@@ -37,6 +37,10 @@
  *                     adds SurrogateCount(N_v, j) = sum over u in N_v with u in
  *                     V_j of |N_u intersect N_v|.  The result is the P x P table
  *                     of those sums by (sender i, counter j), whose total is T.
+ *   or_balanced_cuts  Sec. IV-A: cut V into P sets of consecutive vertices whose
+ *                     costs each come to about 1/P of the total: cut k is the
+ *                     first vertex q whose cost prefix f(0) + ... + f(q-1)
+ *                     reaches k/P of the total (cut 0 = 0, cut P = n).
  *   or_tasks,         The GPU's work decomposition, restated from its
  *   or_task_costs,    definition: each oriented edge becomes one task owned by
  *   or_schedule       the endpoint with the longer list, in a small or a big
@@ -265,6 +269,27 @@ int or_count_parts(int32_t n, const int64_t* off, const int32_t* cols, int32_t n
                 last_proc = j;
             }
         }
+    }
+    return OR_OK;
+}
+
+/*
+ * Sec. IV-A: sum over v in V_k of f(v) ~ (1/P) sum over v of f(v).  With the exclusive prefix
+ * F(q) = f(0) + ... + f(q-1), cut k (0 < k < P) is the first q in [0, n] with
+ * F(q) * P >= k * F(n), i.e. F(q) >= k F(n) / P; cuts[0] = 0 and cuts[P] = n.  The products are
+ * taken in 128 bits.  cuts needs P + 1 entries.
+ */
+int or_balanced_cuts(int32_t n, const uint64_t* f, int32_t P, int32_t* cuts) {
+    if (n < 0 || P < 1) return OR_ERR_INVALID_ARG;
+    unsigned __int128 total = 0;
+    for (int32_t v = 0; v < n; ++v) total += f[v];
+    cuts[0] = 0;
+    cuts[P] = n;
+    for (int32_t k = 1; k < P; ++k) {
+        unsigned __int128 F = 0;  /* F(q), recomputed from 0 for every cut */
+        int32_t q = 0;
+        while (q < n && F * (unsigned)P < total * (unsigned)k) F += f[q++];
+        cuts[k] = q;
     }
     return OR_OK;
 }

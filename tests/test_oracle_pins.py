@@ -334,3 +334,52 @@ def test_partition_bad_cuts():
     for cuts in ([1, n], [0, n - 1], [0, 300, 200, n]):
         with pytest.raises(oracle.OracleError):
             oracle.count_parts(csr, cuts)
+
+
+# ---------------------------------------------------------------- Sec. IV-A balanced cuts
+
+def _prefix(f):
+    F = [0]
+    for x in f:
+        F.append(F[-1] + int(x))
+    return F
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_balanced_cuts_balance_and_minimality(seed):
+    """Every part's cost is below total/P + max f (no cut could move right and keep the parts
+    under their share), and no cut can move left: F(c_k - 1) < k/P of the total <= F(c_k)."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 300))
+    f = rng.integers(0, 50, n).astype(np.uint64)
+    f[rng.random(n) < 0.3] = 0
+    for P in (1, 2, 3, 7, 16, n, n + 5):
+        cuts = oracle.balanced_cuts(f, P).tolist()
+        F = _prefix(f)
+        tot, fmax = F[-1], int(f.max())
+        assert cuts[0] == 0 and cuts[-1] == n and len(cuts) == P + 1
+        assert all(a <= b for a, b in zip(cuts, cuts[1:]))
+        for k in range(P):
+            assert (F[cuts[k + 1]] - F[cuts[k]]) * P <= tot + fmax * P
+        for k in range(1, P):
+            c = cuts[k]
+            assert F[c] * P >= k * tot
+            assert c == 0 or F[c - 1] * P < k * tot
+
+
+def test_balanced_cuts_closed_forms():
+    # equal costs, n = a P: parts of exactly a vertices
+    for a, P in ((5, 4), (1, 9), (13, 3)):
+        assert oracle.balanced_cuts(np.ones(a * P, np.uint64), P).tolist() == list(range(0, a * P + 1, a))
+    # one vertex h carries all the cost: every inner cut sits right after it
+    n, h = 40, 17
+    f = np.zeros(n, np.uint64)
+    f[h] = 1000
+    assert oracle.balanced_cuts(f, 5).tolist() == [0] + [h + 1] * 4 + [n]
+    # no cost at all: the last part takes every vertex
+    assert oracle.balanced_cuts(np.zeros(6, np.uint64), 3).tolist() == [0, 0, 0, 6]
+    # totals beyond 64 bits once multiplied by P
+    big = np.full(4, 2 ** 62, np.uint64)
+    assert oracle.balanced_cuts(big, 4).tolist() == [0, 1, 2, 3, 4]
+    with pytest.raises(oracle.OracleError):
+        oracle.balanced_cuts(np.ones(3, np.uint64), 0)
