@@ -75,6 +75,12 @@ def parse_args():
     p.add_argument("--serve-group-edges", type=int, default=0, help="input edges one slot takes at once (0: default)")
     p.add_argument("--serve-pool", type=int, default=0,
                    help="pre-generated graphs the requests cycle through (default 32, or 256 with --workload serve)")
+    p.add_argument("--no-surrogate", action="store_true",
+                   help="skip the leg that counts the lists over a non-overlapping partition (Sec. IV) from "
+                        "page-locked host memory")
+    p.add_argument("--surrogate-fraction", type=int, default=4,
+                   help="the part-size bound of that leg, as a fraction of the lists (default 4: each part "
+                        "holds at most a quarter of them)")
     p.add_argument("--batch-graphs", type=int, default=0,
                    help="graphs of the batched workload (default: 512 as a leg of a single-graph run, "
                         "4096 with --workload batch)")
@@ -539,6 +545,63 @@ def serve_leg(requests, pool_size, slots=4, group_edges=0):
 
 # --------------------------------------------------------------------------- reference arm
 
+def surrogate_leg(s_dev, d_dev, n, opt, T_ref, stream, fraction=4, reps=3):
+    """Sec. IV's count over a non-overlapping partition (tc_count_surrogate) of the workload's N+
+    lists held in page-locked host memory: no more than 1/fraction of the lists is in device memory
+    at once (two part slices).  Cuts from tc_surrogate_plan with equal list entries per part.  Each
+    call is timed with CUDA events on the stream it runs on (it synchronises that stream), the best
+    of `reps` after one warm-up; the same cuts over device-resident lists and the work-balanced cuts
+    of Sec. IV-F are timed beside it."""
+    import numpy as np
+    import torch
+    import paper_1406_5687_gb300 as tc
+
+    gg = tc.Graph.build(s_dev, d_dev, n, opt)
+    _, off, cols, _ = gg.csr()
+    gg.free()
+    m = int(cols.numel())
+    off_h, cols_h = off.cpu().pin_memory(), cols.cpu().pin_memory()
+    budget = max(4 * m // fraction, 1)
+    t0 = time.perf_counter()
+    cuts = tc.surrogate_plan(off_h, cols_h, part_bytes=budget, fn=tc.TC_FN_LIST)
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    o = off_h.numpy()
+    slices = o[cuts[1:]] - o[cuts[:-1]]
+
+    def timed(of, co, cu):
+        best = None
+        for k in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            T, _tab = tc.count_surrogate(of, co, cu, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if T != T_ref:
+                raise RuntimeError(f"surrogate count {T} != {T_ref}")
+            if k > 0:
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None or ms < best else best
+        return {"ms": best, "value": m / (best / 1e3), "unit": UNIT}
+
+    host = timed(off_h, cols_h, cuts)
+    dev = timed(off, cols, cuts)
+    one = timed(off, cols, np.array([0, n], np.int32))
+    work_cuts = tc.surrogate_plan(off, cols, nparts=len(cuts) - 1, fn=tc.TC_FN_NEW)
+    work = timed(off, cols, work_cuts)
+    ws = o[work_cuts[1:]] - o[work_cuts[:-1]]
+    del off, cols, off_h, cols_h
+    torch.cuda.empty_cache()
+    return {"parts": len(cuts) - 1, "part_bytes_bound": budget, "lists_bytes": 4 * m,
+            "largest_part_bytes": int(4 * slices.max()), "plan_ms": plan_ms,
+            "host_lists": host, "device_lists": dev, "device_lists_one_part": one,
+            "device_lists_work_balanced_cuts": dict(work, largest_part_bytes=int(4 * ws.max())),
+            "h2d_bytes_per_count": int(4 * sum(int(o[b]) - (int(o[a]) & ~3) for a, b in zip(cuts[:-1], cuts[1:]))),
+            "note": "tc_count_surrogate: parts counted one after another, each part's slice copied in "
+                    "(the next copy overlapping this count), every list read in place as a message; "
+                    "value = m_hat / ms of one call, CUDA events on its stream, best of %d after a warm-up; "
+                    "h2d_bytes_per_count counts the slice copies only (messages are read in place)" % reps}
+
+
 def run_reference_batch(args):
     """The oracle, graph by graph, on the first graphs of the batched (or served) workload, a
     bounded sample per step: graphs/s on the host."""
@@ -901,6 +964,10 @@ def run_gpu(args, rank, world, local):
         del tv, _pe, _cc
         gg.free()
 
+    surrogate = None
+    if rank == 0 and not args.no_surrogate:
+        surrogate = surrogate_leg(s_dev, d_dev, spec.n, opt, T_ref, stream, fraction=args.surrogate_fraction)
+
     peak, peak_kind = measured_peaks()
     # The roofline is that of the dominant kernel, k_count_big (the big class of step a7-a8):
     # its algorithmic bytes over its own average duration, timed with CUDA events on the
@@ -947,7 +1014,7 @@ def run_gpu(args, rank, world, local):
                                "note": "m_hat / (cost prefix + schedule + intersection), lists resident"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "work": {"small": alg["small"], "big": alg["big"]}, "wall_s_timed": t_wall,
-                "per_vertex": extras, "batch": batch, "serve": serve}
+                "per_vertex": extras, "surrogate": surrogate, "batch": batch, "serve": serve}
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()

@@ -86,8 +86,10 @@ typedef enum tc_cost_model {
     TC_COST_NEW = 5
 } tc_cost_model;
 
-/* Per-vertex cost functions for tc_vertex_cost (Sec. IV-B, IV-F, V-A). */
-typedef enum tc_cost_fn { TC_FN_ONE = 0, TC_FN_DEGREE = 1, TC_FN_PATRIC = 2, TC_FN_NEW = 3 } tc_cost_fn;
+/* Per-vertex cost functions for tc_vertex_cost (Sec. IV-B, IV-F, V-A).  TC_FN_LIST, f(v) = |N_v|
+ * (the entries of v's list, so parts of equal cost hold about m / P entries each, Sec. IV), is for
+ * tc_surrogate_plan only. */
+typedef enum tc_cost_fn { TC_FN_ONE = 0, TC_FN_DEGREE = 1, TC_FN_PATRIC = 2, TC_FN_NEW = 3, TC_FN_LIST = 4 } tc_cost_fn;
 
 /* Sec. II assumes a simple graph.  SANITIZE drops self-loops and merges repeated
  * or reversed pairs; STRICT returns TC_ERR_INVALID_ARG if it sees any. */
@@ -338,6 +340,69 @@ tc_status tc_count_static(tc_graph_t g, tc_stream_t stream, uint64_t* total_dev)
  * TC_ERR_TIMEOUT; the CUDA context stays usable.  Synchronises `stream`.
  */
 tc_status tc_wait_selftest(int64_t spin_limit, tc_stream_t stream);
+
+/* ------------------------------------------------- non-overlapping partition (Sec. IV) */
+
+/*
+ * Count over a non-overlapping partition, for N+ lists that need not fit in device memory
+ * (Sec. IV, the space-efficient algorithm).  The input is the oriented graph itself, in the
+ * layout of tc_graph_csr: N_v = cols[off[v] .. off[v+1]), each list strictly ascending, every
+ * triangle appearing as (v, u, w) with u, w in N_v and w in N_u (Fig. 1's orientation).
+ *
+ * The vertices are split into the sets of consecutive ids V_j = [cuts[j], cuts[j+1]) of Def. 1;
+ * part j's partition G_j is the lists N_u, u in V_j, one contiguous slice of cols.  Parts
+ * part_lo .. part_hi-1 are counted one after another on this GPU: part j's slice is copied to
+ * device memory (the copy of the next part overlapping the count of this one), and every list
+ * N_v holding an entry in V_j is a data message to part j, sent once (the surrogate approach of
+ * Sec. IV-C), which adds SurrogateCount(N_v, j) = sum over u in N_v ∩ V_j of |N_u ∩ N_v|
+ * (Fig. 2).  Messages are read in place.  Device memory holds the offsets, two per-vertex
+ * cursors (8 n bytes), the work items (16 (n + m / 256) bytes) and two part slices, never all
+ * of cols.
+ *   off        host or device, n + 1 int64: off[0] = 0, non-decreasing, off[n] = m.
+ *   cols       host or device, m int32.  Host lists are read over the host link; page-locked
+ *              memory is read in place, pageable memory is page-locked for the call.
+ *   n, m       vertices (0 <= n < 2^31 - 1) and list entries.
+ *   cuts       host, nparts + 1 int32: cuts[0] = 0, cuts[nparts] = n, non-decreasing (empty
+ *              sets allowed); 1 <= nparts <= TC_SURROGATE_MAX_PARTS.
+ *   part_lo, part_hi  the receiving parts counted: 0 <= part_lo <= part_hi <= nparts.  Disjoint
+ *              ranges counted separately (on several GPUs, or calls) add up to the full count.
+ *   opt        NULL for defaults; only the allocator hooks and hbm_budget_bytes are used.
+ *   table      host, nparts * nparts uint64, or NULL: table[i * nparts + j] = the sum over v in
+ *              V_i of SurrogateCount(N_v, j), the triangles whose two lowest vertices (in the
+ *              orientation's order) lie in V_i and V_j; columns outside [part_lo, part_hi) are 0.
+ *   total      host; the sum of the table: T when the range covers every part.
+ * Errors: TC_ERR_INVALID_ARG (bad sizes or cuts, off not as stated, a list not strictly
+ * ascending), TC_ERR_VERTEX_RANGE (a list entry outside [0, n), found when the range covers the
+ * lists' entries), TC_ERR_UNSUPPORTED (a part slice of 2^32 - 8 or more entries), TC_ERR_OOM,
+ * TC_ERR_BUDGET, TC_ERR_CUDA.  Synchronises `stream`.
+ */
+#define TC_SURROGATE_MAX_PARTS 1024
+tc_status tc_count_surrogate(const int64_t* off, const int32_t* cols, int32_t n, int64_t m, const int32_t* cuts,
+                             int32_t nparts, int32_t part_lo, int32_t part_hi, const tc_options* opt,
+                             tc_stream_t stream, uint64_t* table, uint64_t* total);
+
+/*
+ * Cuts for tc_count_surrogate (Sec. IV-A): with a per-vertex cost f, cuts[k] is the first vertex q
+ * whose exclusive prefix F[q] = f(0) + ... + f(q-1) reaches ceil(k F[n] / P); cuts[0] = 0 and
+ * cuts[P] = n.  Every part then holds about 1 / P of the cost.
+ *   off, cols, n, m  as for tc_count_surrogate (cols is read only for DEGREE, PATRIC and NEW).
+ *   fn         a tc_cost_fn.  TC_FN_NEW (Sec. IV-F): f(u) = sum over the lists N_v holding u of
+ *              (|N_u| + |N_v|), the work u's part does for u: parts of equal work, for parts
+ *              counted on several GPUs.  TC_FN_LIST: f(v) = |N_v|: parts of equal size, the
+ *              fewest parts within a memory bound.  ONE, DEGREE (d_v) and PATRIC (Sec. IV-B)
+ *              as for tc_vertex_cost.
+ *   nparts     > 0: P = nparts.  0: the smallest P in [ceil(4 m / part_bytes), max_parts] whose
+ *              cuts keep every part's slice within part_bytes.
+ *   part_bytes bytes of one part's slice (4 per entry); 0 = no limit (needs nparts > 0).
+ *   max_parts  upper bound on P when nparts = 0 (<= TC_SURROGATE_MAX_PARTS).
+ *   cuts       host, receives P + 1 int32 (capacity nparts + 1, or max_parts + 1).
+ *   nparts_out host; receives P.
+ * Errors: TC_ERR_BUDGET (no P within the bounds fits; the last cuts tried are written),
+ * TC_ERR_INVALID_ARG, TC_ERR_VERTEX_RANGE, TC_ERR_OOM, TC_ERR_CUDA.  Synchronises `stream`.
+ */
+tc_status tc_surrogate_plan(const int64_t* off, const int32_t* cols, int32_t n, int64_t m, int32_t fn,
+                            int32_t nparts, int64_t part_bytes, int32_t max_parts, tc_stream_t stream, int32_t* cuts,
+                            int32_t* nparts_out);
 
 /* ------------------------------------------------------------------ batch */
 

@@ -13,10 +13,11 @@ import ctypes
 
 from . import _lib
 from ._lib import (TC_COST_DEGREE, TC_COST_EDGE, TC_COST_MERGE, TC_COST_NEW, TC_COST_ONE, TC_COST_PATRIC,
-                   TC_FN_DEGREE, TC_FN_NEW, TC_FN_ONE, TC_FN_PATRIC, TC_INPUT_SANITIZE, TC_INPUT_STRICT, TcError,
+                   TC_FN_DEGREE, TC_FN_LIST, TC_FN_NEW, TC_FN_ONE, TC_FN_PATRIC, TC_INPUT_SANITIZE, TC_INPUT_STRICT, TcError,
                    default_options)
 
-__all__ = ["Graph", "Batch", "autotune", "Server", "TcError", "default_options", "load", "version", "kernel_launches"]
+__all__ = ["Graph", "Batch", "autotune", "Server", "TcError", "default_options", "load", "version", "kernel_launches",
+           "count_surrogate", "surrogate_plan"]
 
 
 def load():
@@ -244,6 +245,63 @@ class Graph:
         cols = _view(c.value, mh, "<i4").clone()
         tasks = _view(t.value, 4 * T, "<i4").clone().view(-1, 4)
         return deg, off, cols, tasks
+
+
+def _array_ptr(a, dtype_name: str):
+    """(pointer, length, keepalive) of a numpy array or torch tensor (host, pinned host or CUDA)."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != getattr(torch, dtype_name):
+                raise TypeError(f"expected a {dtype_name} tensor")
+            t = a.contiguous()
+            return ctypes.c_void_p(t.data_ptr()), int(t.numel()), t
+    except ImportError:  # pragma: no cover
+        pass
+    import numpy as np
+    x = np.ascontiguousarray(a, dtype=getattr(np, dtype_name))
+    return x.ctypes.data_as(ctypes.c_void_p), int(x.size), x
+
+
+def surrogate_plan(off, cols, nparts: int = 0, part_bytes: int = 0, fn: int = TC_FN_NEW,
+                   max_parts: int = _lib.TC_SURROGATE_MAX_PARTS, stream=None):
+    """Cuts (int32 numpy array of P + 1 vertex ids) of Sec. IV-A's cost-balanced non-overlapping
+    partition of the oriented lists (off, cols) under the per-vertex cost `fn` (TC_FN_NEW: equal
+    work, Sec. IV-F; TC_FN_LIST: equal list entries).  nparts > 0 fixes P; nparts = 0 picks the
+    smallest P whose parts' list slices each fit in part_bytes."""
+    import numpy as np
+    op, n1, ko = _array_ptr(off, "int64")
+    cp, m, kc = _array_ptr(cols, "int32")
+    cap = (nparts if nparts > 0 else max_parts) + 1
+    cuts = np.zeros(cap, np.int32)
+    P = ctypes.c_int32()
+    rc = load().tc_surrogate_plan(op, cp, n1 - 1, m, int(fn), int(nparts), int(part_bytes), int(max_parts),
+                                  _stream(stream), cuts.ctypes.data_as(ctypes.c_void_p), ctypes.byref(P))
+    del ko, kc
+    _lib.check(rc, "tc_surrogate_plan")
+    return cuts[:P.value + 1].copy()
+
+
+def count_surrogate(off, cols, cuts, part_lo: int = 0, part_hi: int | None = None,
+                    options: _lib.Options | None = None, stream=None):
+    """(total, table) of the count over the non-overlapping partition `cuts` (Sec. IV):
+    table[i, j] sums SurrogateCount(N_v, j) over v in V_i, for the receiving parts
+    part_lo <= j < part_hi (all parts by default); total is the table's sum."""
+    import numpy as np
+    op, n1, ko = _array_ptr(off, "int64")
+    cp, m, kc = _array_ptr(cols, "int32")
+    cu = np.ascontiguousarray(cuts, dtype=np.int32)
+    P = len(cu) - 1
+    hi = P if part_hi is None else int(part_hi)
+    table = np.zeros(max(P, 1) * max(P, 1), np.uint64)
+    t = ctypes.c_uint64()
+    opt = ctypes.byref(options) if options is not None else None
+    rc = load().tc_count_surrogate(op, cp if m else None, n1 - 1, m, cu.ctypes.data_as(ctypes.c_void_p), P,
+                                   int(part_lo), hi, opt, _stream(stream), table.ctypes.data_as(ctypes.c_void_p),
+                                   ctypes.byref(t))
+    del ko, kc
+    _lib.check(rc, "tc_count_surrogate")
+    return int(t.value), table[:P * P].reshape(P, P)
 
 
 from .batch import Batch, autotune  # noqa: E402

@@ -22,10 +22,11 @@ STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_VERTEX_RANGE", 3
 (TC_ERR_INVALID_ARG, TC_ERR_VERTEX_RANGE, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_BUDGET,
  TC_ERR_UNSUPPORTED, TC_ERR_CANCELLED) = range(1, 9)
 TC_COST_EDGE, TC_COST_MERGE, TC_COST_ONE, TC_COST_DEGREE, TC_COST_PATRIC, TC_COST_NEW = range(6)
-TC_FN_ONE, TC_FN_DEGREE, TC_FN_PATRIC, TC_FN_NEW = range(4)
+TC_FN_ONE, TC_FN_DEGREE, TC_FN_PATRIC, TC_FN_NEW, TC_FN_LIST = range(5)
 TC_INPUT_SANITIZE, TC_INPUT_STRICT = 0, 1
 TC_COUNT_STATIC_MAX_TASKS = 1 << 19  # include/tc.h
 TC_TRIM_MIN_ENTRIES = 16  # include/tc.h
+TC_SURROGATE_MAX_PARTS = 1024  # include/tc.h
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -125,6 +126,11 @@ SIGNATURES = {
     "tc_kernel_launches": (ctypes.c_int64, []),
     "tc_count_static": (ctypes.c_int, [P, P, P]),
     "tc_wait_selftest": (ctypes.c_int, [ctypes.c_int64, P]),
+    "tc_count_surrogate": (ctypes.c_int, [P, P, ctypes.c_int32, ctypes.c_int64, P, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.POINTER(Options), P, P,
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "tc_surrogate_plan": (ctypes.c_int, [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int64, ctypes.c_int32, P, P, ctypes.POINTER(ctypes.c_int32)]),
     "tc_batch_build": (ctypes.c_int, [P, P, P, P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(Options), P,
                                       ctypes.POINTER(P)]),
     "tc_batch_run": (ctypes.c_int, [P, P, P]),

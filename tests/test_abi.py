@@ -49,3 +49,38 @@ def test_host_only_calls():
         assert lib.tc_build(None, None, 0, 10, ctypes.byref(bad), None, ctypes.byref(h)) == _lib.TC_ERR_INVALID_ARG
     assert lib.tc_count(None, None, None) == _lib.TC_ERR_INVALID_ARG
     lib.tc_free(None)
+
+
+def test_surrogate_argument_checks():
+    """Bad sizes, ranges and cuts are refused before any device work."""
+    import numpy as np
+    from paper_1406_5687_gb300 import _lib
+    lib = _lib.load()
+    off = np.zeros(11, np.int64)
+    t = ctypes.c_uint64()
+    P = ctypes.c_int32()
+    o = off.ctypes.data_as(ctypes.c_void_p)
+
+    def count(cuts, lo=0, hi=None, n=10, m=0):
+        c = np.asarray(cuts, np.int32)
+        return lib.tc_count_surrogate(o, None, n, m, c.ctypes.data_as(ctypes.c_void_p), len(c) - 1, lo,
+                                      len(c) - 1 if hi is None else hi, None, None, None, ctypes.byref(t))
+
+    for cuts in ([1, 10], [0, 9], [0, 6, 5, 10], [0]):
+        assert count(cuts) == _lib.TC_ERR_INVALID_ARG, cuts
+    assert count([0, 5, 10], lo=1, hi=0) == _lib.TC_ERR_INVALID_ARG
+    assert count([0, 5, 10], lo=0, hi=3) == _lib.TC_ERR_INVALID_ARG
+    assert count([0, 10], n=-1) == _lib.TC_ERR_INVALID_ARG
+    assert count([0, 10], m=5) == _lib.TC_ERR_INVALID_ARG  # entries but no cols
+    too_many = np.linspace(0, 10, _lib.TC_SURROGATE_MAX_PARTS + 2).astype(np.int32)
+    assert count(too_many) == _lib.TC_ERR_INVALID_ARG
+    cuts = np.zeros(8, np.int32)
+    cp = cuts.ctypes.data_as(ctypes.c_void_p)
+    # nparts = 0 needs a part size; negative sizes are refused
+    new = _lib.TC_FN_NEW
+    assert lib.tc_surrogate_plan(o, None, 10, 0, new, 0, 0, 7, None, cp, ctypes.byref(P)) == _lib.TC_ERR_INVALID_ARG
+    assert lib.tc_surrogate_plan(o, None, 10, 0, new, 2, -1, 7, None, cp, ctypes.byref(P)) == _lib.TC_ERR_INVALID_ARG
+    assert lib.tc_surrogate_plan(o, None, 10, 0, new, _lib.TC_SURROGATE_MAX_PARTS + 1, 0, 7, None, cp,
+                                 ctypes.byref(P)) == _lib.TC_ERR_INVALID_ARG
+    for fn in (-1, _lib.TC_FN_LIST + 1):
+        assert lib.tc_surrogate_plan(o, None, 10, 0, fn, 2, 0, 7, None, cp, ctypes.byref(P)) == _lib.TC_ERR_INVALID_ARG
