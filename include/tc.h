@@ -382,7 +382,7 @@ tc_status tc_count_surrogate(const int64_t* off, const int32_t* cols, int32_t n,
                              tc_stream_t stream, uint64_t* table, uint64_t* total);
 
 /*
- * Cuts for tc_count_surrogate (Sec. IV-A): with a per-vertex cost f, cuts[k] is the first vertex q
+ * Cuts for tc_count_surrogate (Sec. IV-B): with a per-vertex cost f, cuts[k] is the first vertex q
  * whose exclusive prefix F[q] = f(0) + ... + f(q-1) reaches ceil(k F[n] / P); cuts[0] = 0 and
  * cuts[P] = n.  Every part then holds about 1 / P of the cost.
  *   off, cols, n, m  as for tc_count_surrogate (cols is read only for DEGREE, PATRIC and NEW).

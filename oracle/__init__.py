@@ -172,7 +172,7 @@ def count_parts(csr: OrientedCSR, cuts) -> np.ndarray:
 
 
 def balanced_cuts(f, P: int) -> np.ndarray:
-    """Sec. IV-A: cuts (P + 1 int32) of V into P sets of consecutive vertices of about equal cost:
+    """Sec. IV-B: cuts (P + 1 int32) of V into P sets of consecutive vertices of about equal cost:
     cut k is the first q whose cost prefix f(0) + ... + f(q-1) reaches k/P of the total."""
     L = _load()
     f = np.ascontiguousarray(f, dtype=np.uint64)

@@ -37,7 +37,7 @@
  *                     adds SurrogateCount(N_v, j) = sum over u in N_v with u in
  *                     V_j of |N_u intersect N_v|.  The result is the P x P table
  *                     of those sums by (sender i, counter j), whose total is T.
- *   or_balanced_cuts  Sec. IV-A: cut V into P sets of consecutive vertices whose
+ *   or_balanced_cuts  Sec. IV-B: cut V into P sets of consecutive vertices whose
  *                     costs each come to about 1/P of the total: cut k is the
  *                     first vertex q whose cost prefix f(0) + ... + f(q-1)
  *                     reaches k/P of the total (cut 0 = 0, cut P = n).
@@ -274,7 +274,7 @@ int or_count_parts(int32_t n, const int64_t* off, const int32_t* cols, int32_t n
 }
 
 /*
- * Sec. IV-A: sum over v in V_k of f(v) ~ (1/P) sum over v of f(v).  With the exclusive prefix
+ * Sec. IV-B: sum over v in V_k of f(v) ~ (1/P) sum over v of f(v).  With the exclusive prefix
  * F(q) = f(0) + ... + f(q-1), cut k (0 < k < P) is the first q in [0, n] with
  * F(q) * P >= k * F(n), i.e. F(q) >= k F(n) / P; cuts[0] = 0 and cuts[P] = n.  The products are
  * taken in 128 bits.  cuts needs P + 1 entries.

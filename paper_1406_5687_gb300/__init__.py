@@ -265,7 +265,7 @@ def _array_ptr(a, dtype_name: str):
 
 def surrogate_plan(off, cols, nparts: int = 0, part_bytes: int = 0, fn: int = TC_FN_NEW,
                    max_parts: int = _lib.TC_SURROGATE_MAX_PARTS, stream=None):
-    """Cuts (int32 numpy array of P + 1 vertex ids) of Sec. IV-A's cost-balanced non-overlapping
+    """Cuts (int32 numpy array of P + 1 vertex ids) of Sec. IV-B's cost-balanced non-overlapping
     partition of the oriented lists (off, cols) under the per-vertex cost `fn` (TC_FN_NEW: equal
     work, Sec. IV-F; TC_FN_LIST: equal list entries).  nparts > 0 fixes P; nparts = 0 picks the
     smallest P whose parts' list slices each fit in part_bytes."""

@@ -22,7 +22,7 @@
 // units.  Hits go to a per-block counter of the sender's part i; each block adds its counters to
 // table[i][j] once, at its end.
 //
-// Planning (Sec. IV-A): cuts[k] is the first vertex whose exclusive prefix of a per-vertex cost f
+// Planning (Sec. IV-B): cuts[k] is the first vertex whose exclusive prefix of a per-vertex cost f
 // reaches k / P of the total, so every part gets about 1 / P of it.  With Sec. IV-F's f(u) = sum
 // over the lists N_v holding u of (d^_u + d^_v), the work part j does for u, the parts take equal
 // work; with f(v) = |N_v| they hold equal shares of the lists (about m / P entries each).

@@ -4,7 +4,7 @@ tc_count_surrogate's P x P table (sender part i, receiving part j) must equal th
 SurrogateCount table bit-exactly, for every cut pattern (one part, balanced parts, empty parts,
 one vertex per part), every memory kind of the lists (pageable host, page-locked host, device,
 device off a 16-byte boundary) and every range of receiving parts.  tc_surrogate_plan's cuts must
-equal the oracle's Sec. IV-A cuts over the Sec. IV-F cost.
+equal the oracle's Sec. IV-B cuts over the Sec. IV-F cost.
 """
 import numpy as np
 import pytest

@@ -336,7 +336,7 @@ def test_partition_bad_cuts():
             oracle.count_parts(csr, cuts)
 
 
-# ---------------------------------------------------------------- Sec. IV-A balanced cuts
+# ---------------------------------------------------------------- Sec. IV-B balanced cuts
 
 def _prefix(f):
     F = [0]
