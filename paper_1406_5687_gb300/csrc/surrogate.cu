@@ -29,6 +29,8 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "graph.cuh"
@@ -603,16 +605,70 @@ struct SDev {
     unsigned long long max_entries;
 };
 
-// Device-readable views of the caller's lists for one call.  Pageable host memory is
-// registered (page-locked) for the call and released at its end.
+// Pageable host lists are page-locked for the duration of a call.  Calls may overlap (several
+// threads, the same lists), so the library's registrations are counted: a call inside a range
+// that another call registered takes a reference, the last call to finish unregisters, and no
+// call releases memory another still reads.  A range that only partly overlaps a registered one
+// is refused.
+std::mutex g_reg_mu;
+struct RegEntry {
+    size_t bytes;
+    int refs;
+};
+std::map<uintptr_t, RegEntry>& registrations() {
+    static std::map<uintptr_t, RegEntry> m;
+    return m;
+}
+
+// Page-lock [p, p + bytes) or take a reference on a registration covering it; *key receives the
+// registration to release (0: none needed, the caller's memory was already page-locked).
+tc_status acquire_host(const void* p, size_t bytes, uintptr_t* key) {
+    *key = 0;
+    const uintptr_t a = (uintptr_t)p, b = a + bytes;
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    auto& m = registrations();
+    auto it = m.upper_bound(a);  // first registration starting after a
+    if (it != m.begin()) {
+        auto pr = std::prev(it);
+        const uintptr_t e = pr->first + pr->second.bytes;
+        if (e > a) {
+            if (b > e) return TC_ERR_INVALID_ARG;  // runs past the registered range
+            ++pr->second.refs;
+            *key = pr->first;
+            return TC_OK;
+        }
+    }
+    if (it != m.end() && it->first < b) return TC_ERR_INVALID_ARG;  // a registered range starts inside
+    if (pinned_device_view(p)) return TC_OK;  // page-locked by the caller
+    cudaError_t err = cudaHostRegister(const_cast<void*>(p), bytes, cudaHostRegisterPortable | cudaHostRegisterMapped);
+    if (err != cudaSuccess) {
+        (void)cudaGetLastError();
+        return err == cudaErrorMemoryAllocation ? TC_ERR_OOM : TC_ERR_CUDA;
+    }
+    m[a] = RegEntry{bytes, 1};
+    *key = a;
+    return TC_OK;
+}
+
+void release_host(uintptr_t key) {
+    if (!key) return;
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    auto& m = registrations();
+    auto it = m.find(key);
+    if (it == m.end()) return;
+    if (--it->second.refs == 0) {
+        cudaHostUnregister((void*)key);
+        m.erase(it);
+    }
+}
+
+// Device-readable views of the caller's lists for one call.
 struct Lists {
     const int64_t* off_host = nullptr;  // non-null when off is host memory
     const int32_t* msrc = nullptr;      // device-readable cols
     bool cols_device = false;
-    const void* registered = nullptr;
-    ~Lists() {
-        if (registered) cudaHostUnregister(const_cast<void*>(registered));
-    }
+    uintptr_t registered = 0;  // registration this call holds (release_host)
+    ~Lists() { release_host(registered); }
 };
 
 // Declared after a Lists, so that no kernel still reads the lists when they are released.
@@ -628,17 +684,9 @@ tc_status device_cols(const int32_t* cols, int64_t m, Lists* L) {
         L->cols_device = true;
         return TC_OK;
     }
+    TC_TRY(acquire_host(cols, (size_t)m * 4, &L->registered));
     const void* pin = pinned_device_view(cols);
-    if (!pin) {
-        cudaError_t e = cudaHostRegister(const_cast<int32_t*>(cols), (size_t)m * 4, cudaHostRegisterDefault);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            return e == cudaErrorMemoryAllocation ? TC_ERR_OOM : TC_ERR_CUDA;
-        }
-        L->registered = cols;
-        pin = pinned_device_view(cols);
-        if (!pin) return TC_ERR_CUDA;
-    }
+    if (!pin) return TC_ERR_CUDA;
     L->msrc = (const int32_t*)pin;
     return TC_OK;
 }

@@ -244,3 +244,31 @@ def test_budget_and_allocator_hooks():
     assert e.value.code == _lib.TC_ERR_BUDGET
     total, tab = tc.count_surrogate(csr.off, csr.cols, cuts, options=tc.default_options(hbm_budget_bytes=1 << 30))
     assert np.array_equal(tab, _expected("cl_200k", cuts))
+
+
+def test_concurrent_calls_on_the_same_pageable_lists():
+    """Threads counting the same pageable host lists at once, each on its own stream: the lists
+    stay page-locked until the last call ends, and every call gets the oracle's table."""
+    import threading
+    csr = CSR["cl_200k"]
+    cuts = oracle.balanced_cuts(np.diff(csr.off).astype(np.uint64), 3)
+    exp = _expected("cl_200k", cuts)
+    ok, errors = [], []
+
+    def worker():
+        try:
+            torch.cuda.set_device(0)
+            st = torch.cuda.Stream()
+            for _ in range(3):
+                _, tab = tc.count_surrogate(csr.off, csr.cols, cuts, stream=st)
+                ok.append(np.array_equal(tab, exp))
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker) for _ in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    assert ok == [True] * 12
