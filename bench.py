@@ -220,6 +220,20 @@ def stored_traffic(workload):
     return rec.get("dram_bytes_per_launch")
 
 
+def stored_surrogate_traffic():
+    """DRAM bytes (read + write) of k_surrogate_count over the parts of one host-list call of the
+    bench's surrogate leg, from the ncu capture in profiles/, or None when surrogate.cu has changed
+    since it was taken."""
+    path = os.path.join(ROOT, "profiles", "k_surrogate_count_cl_traffic.json")
+    src = os.path.join(ROOT, "paper_1406_5687_gb300", "csrc", "surrogate.cu")
+    try:
+        rec = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    return rec.get("dram_bytes_per_call") if rec.get("surrogate_cu_sha256") == sha else None
+
+
 def algorithmic_bytes(g, opt):
     """Bytes the count kernels must move per count if nothing were cached, per class.
 
@@ -584,6 +598,10 @@ def surrogate_leg(s_dev, d_dev, n, opt, T_ref, stream, fraction=4, reps=3):
         return {"ms": best, "value": m / (best / 1e3), "unit": UNIT}
 
     host = timed(off_h, cols_h, cuts)
+    # one more call with the work counters and per-kernel CUDA events (outside the timed best-of)
+    T, _tab, st = tc.count_surrogate(off_h, cols_h, cuts, stream=stream, stats=True)
+    if T != T_ref:
+        raise RuntimeError("surrogate count with counters disagrees")
     dev = timed(off, cols, cuts)
     one = timed(off, cols, np.array([0, n], np.int32))
     work_cuts = tc.surrogate_plan(off, cols, nparts=len(cuts) - 1, fn=tc.TC_FN_NEW)
@@ -591,11 +609,23 @@ def surrogate_leg(s_dev, d_dev, n, opt, T_ref, stream, fraction=4, reps=3):
     ws = o[work_cuts[1:]] - o[work_cuts[:-1]]
     del off, cols, off_h, cols_h
     torch.cuda.empty_cache()
+    # k_surrogate_count's algorithmic bytes per call: per item its 16-byte record and the staged
+    # message (4 per entry); per (v, u) pair -- m_hat of them, each oriented edge once -- the entry u
+    # (4) and N_u's offsets (16); and the resident entries streamed after trimming (4 each)
+    alg = 16 * st["items"] + 4 * st["staged"] + 20 * m + 4 * st["streamed"]
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (st["count_ms"] / 1e3) / 1e9
+    roofline = {"kernel": "k_surrogate_count (SurrogateCount of Fig. 2, all parts of one call)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"hbm_gbs of {peak_kind}", "traffic": stored_surrogate_traffic(),
+                "algorithmic_bytes": alg, "kernel_ms": st["count_ms"], "route_ms": st["route_ms"],
+                "work": st}
     return {"parts": len(cuts) - 1, "part_bytes_bound": budget, "lists_bytes": 4 * m,
             "largest_part_bytes": int(4 * slices.max()), "plan_ms": plan_ms,
             "host_lists": host, "device_lists": dev, "device_lists_one_part": one,
             "device_lists_work_balanced_cuts": dict(work, largest_part_bytes=int(4 * ws.max())),
             "h2d_bytes_per_count": int(4 * sum(int(o[b]) - (int(o[a]) & ~3) for a, b in zip(cuts[:-1], cuts[1:]))),
+            "roofline": roofline,
             "note": "tc_count_surrogate: parts counted one after another, each part's slice copied in "
                     "(the next copy overlapping this count), every list read in place as a message; "
                     "value = m_hat / ms of one call, CUDA events on its stream, best of %d after a warm-up; "

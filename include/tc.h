@@ -371,15 +371,28 @@ tc_status tc_wait_selftest(int64_t spin_limit, tc_stream_t stream);
  *              V_i of SurrogateCount(N_v, j), the triangles whose two lowest vertices (in the
  *              orientation's order) lie in V_i and V_j; columns outside [part_lo, part_hi) are 0.
  *   total      host; the sum of the table: T when the range covers every part.
+ *   stats      host, or NULL: filled with the work done (counting it adds one atomic per warp
+ *              batch, and CUDA events around every kernel).
  * Errors: TC_ERR_INVALID_ARG (bad sizes or cuts, off not as stated, a list not strictly
- * ascending), TC_ERR_VERTEX_RANGE (a list entry outside [0, n), found when the range covers the
- * lists' entries), TC_ERR_UNSUPPORTED (a part slice of 2^32 - 8 or more entries), TC_ERR_OOM,
- * TC_ERR_BUDGET, TC_ERR_CUDA.  Synchronises `stream`.
+ * ascending, pageable host lists that partly overlap lists another call has page-locked),
+ * TC_ERR_VERTEX_RANGE (a list entry outside [0, n), found when the range covers the lists'
+ * entries), TC_ERR_UNSUPPORTED (a part slice of 2^32 - 8 or more entries), TC_ERR_OOM,
+ * TC_ERR_BUDGET, TC_ERR_CUDA.  Synchronises `stream`.  Calls may run at once on other streams
+ * and threads, on the same lists.
  */
 #define TC_SURROGATE_MAX_PARTS 1024
+typedef struct tc_surrogate_stats {
+    int64_t items;         /* work items: runs of at most 256 entries of one message in one part */
+    int64_t staged;        /* message entries staged into shared memory (X of Fig. 2) */
+    int64_t streamed;      /* resident list entries streamed through them, after trimming each
+                              N_u to its message's [first, last] range */
+    int64_t copied_bytes;  /* part slices copied into device memory */
+    float route_ms;        /* CUDA-event time of the routing kernels, all parts */
+    float count_ms;        /* CUDA-event time of the count kernels, all parts */
+} tc_surrogate_stats;
 tc_status tc_count_surrogate(const int64_t* off, const int32_t* cols, int32_t n, int64_t m, const int32_t* cuts,
                              int32_t nparts, int32_t part_lo, int32_t part_hi, const tc_options* opt,
-                             tc_stream_t stream, uint64_t* table, uint64_t* total);
+                             tc_stream_t stream, uint64_t* table, uint64_t* total, tc_surrogate_stats* stats);
 
 /*
  * Cuts for tc_count_surrogate (Sec. IV-B): with a per-vertex cost f, cuts[k] is the first vertex q

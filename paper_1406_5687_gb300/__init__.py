@@ -283,10 +283,12 @@ def surrogate_plan(off, cols, nparts: int = 0, part_bytes: int = 0, fn: int = TC
 
 
 def count_surrogate(off, cols, cuts, part_lo: int = 0, part_hi: int | None = None,
-                    options: _lib.Options | None = None, stream=None):
+                    options: _lib.Options | None = None, stream=None, stats: bool = False):
     """(total, table) of the count over the non-overlapping partition `cuts` (Sec. IV):
     table[i, j] sums SurrogateCount(N_v, j) over v in V_i, for the receiving parts
-    part_lo <= j < part_hi (all parts by default); total is the table's sum."""
+    part_lo <= j < part_hi (all parts by default); total is the table's sum.  With stats=True a
+    third element holds the work done (items, staged and streamed entries, copied bytes, kernel
+    times)."""
     import numpy as np
     op, n1, ko = _array_ptr(off, "int64")
     cp, m, kc = _array_ptr(cols, "int32")
@@ -296,11 +298,14 @@ def count_surrogate(off, cols, cuts, part_lo: int = 0, part_hi: int | None = Non
     table = np.zeros(max(P, 1) * max(P, 1), np.uint64)
     t = ctypes.c_uint64()
     opt = ctypes.byref(options) if options is not None else None
+    st = _lib.SurrogateStats()
     rc = load().tc_count_surrogate(op, cp if m else None, n1 - 1, m, cu.ctypes.data_as(ctypes.c_void_p), P,
                                    int(part_lo), hi, opt, _stream(stream), table.ctypes.data_as(ctypes.c_void_p),
-                                   ctypes.byref(t))
+                                   ctypes.byref(t), ctypes.byref(st) if stats else None)
     del ko, kc
     _lib.check(rc, "tc_count_surrogate")
+    if stats:
+        return int(t.value), table[:P * P].reshape(P, P), st.as_dict()
     return int(t.value), table[:P * P].reshape(P, P)
 
 

@@ -87,6 +87,14 @@ class TuneReport(ctypes.Structure):
                 ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float)]
 
 
+class SurrogateStats(ctypes.Structure):
+    _fields_ = [("items", ctypes.c_int64), ("staged", ctypes.c_int64), ("streamed", ctypes.c_int64),
+                ("copied_bytes", ctypes.c_int64), ("route_ms", ctypes.c_float), ("count_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Result(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_uint64), ("total", ctypes.c_uint64), ("status", ctypes.c_int32),
                 ("slot", ctypes.c_int32), ("group", ctypes.c_int32), ("reserved", ctypes.c_int32),
@@ -128,7 +136,7 @@ SIGNATURES = {
     "tc_wait_selftest": (ctypes.c_int, [ctypes.c_int64, P]),
     "tc_count_surrogate": (ctypes.c_int, [P, P, ctypes.c_int32, ctypes.c_int64, P, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.POINTER(Options), P, P,
-                                          ctypes.POINTER(ctypes.c_uint64)]),
+                                          ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(SurrogateStats)]),
     "tc_surrogate_plan": (ctypes.c_int, [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int64, ctypes.c_int32, P, P, ctypes.POINTER(ctypes.c_int32)]),
     "tc_batch_build": (ctypes.c_int, [P, P, P, P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(Options), P,

@@ -70,6 +70,7 @@ struct SArgs {
     int32_t c_lo, c_hi;                 // V_j
     int32_t nparts, j;
     unsigned long long* table;          // device, nparts * nparts
+    unsigned long long* counters;       // device (staged, streamed) entries, or null
     DevStatus* st;
 };
 
@@ -186,6 +187,10 @@ __device__ uint32_t s_batch(const SArgs& a, bool valid, uint32_t u, uint32_t reg
         reg = __shfl_sync(kFull, reg, src);
         len = lane < na ? gl : 0u;
     }
+    if (a.counters) {
+        const uint32_t tot = warp_sum(len);
+        if (lane == 0) atomicAdd(&a.counters[1], (unsigned long long)tot);
+    }
     const uint32_t units = len != 0u ? (((ps & 3u) + len + 3u) >> 2) : 0u;
     const uint32_t uincl = warp_inclusive_scan(units, lane);
     const uint32_t ustart = uincl - units;
@@ -240,6 +245,7 @@ __device__ uint32_t s_batch(const SArgs& a, bool valid, uint32_t u, uint32_t reg
 // strictly (the entry before a staged one is in the lane below, or reloaded by lane 0).
 __device__ __forceinline__ void s_stage(const SArgs& a, uint32_t* __restrict__ tbl, long long xb, uint32_t pos0,
                                         uint32_t len, uint32_t excl, uint32_t reg, uint32_t tot, int lane) {
+    if (a.counters && lane == 0) atomicAdd(&a.counters[0], (unsigned long long)tot);
     uint32_t before = 0u;
     for (uint32_t base = 0; base < tot; base += 32u) {
         const uint32_t rel = excl - base;
@@ -406,7 +412,8 @@ __global__ void __launch_bounds__(kRouteBlock) k_surrogate_route(const int64_t* 
                                                                  int32_t c_lo, int32_t c_hi, uint32_t* cur,
                                                                  int32_t* nx, SItem* items,
                                                                  unsigned long long* n_items,
-                                                                 unsigned long long cap, DevStatus* st) {
+                                                                 unsigned long long cap,
+                                                                 unsigned long long* items_total, DevStatus* st) {
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -458,7 +465,10 @@ __global__ void __launch_bounds__(kRouteBlock) k_surrogate_route(const int64_t* 
         const uint32_t incl = warp_inclusive_scan(nit, lane);
         const uint32_t tot = __shfl_sync(kFull, incl, 31);
         unsigned long long wb = 0;
-        if (lane == 31 && tot) wb = atomicAdd(n_items, (unsigned long long)tot);
+        if (lane == 31 && tot) {
+            wb = atomicAdd(n_items, (unsigned long long)tot);
+            if (items_total) atomicAdd(items_total, (unsigned long long)tot);
+        }
         wb = __shfl_sync(kFull, wb, 31);
         if (tot && wb + tot > cap) {
             if (lane == 0) set_error(st, TC_ERR_INVALID_ARG, -1);
@@ -603,6 +613,7 @@ struct SDev {
     unsigned long long n_items;
     unsigned long long claim;
     unsigned long long max_entries;
+    unsigned long long counters[3];  // staged, streamed, items (with stats)
 };
 
 // Pageable host lists are page-locked for the duration of a call.  Calls may overlap (several
@@ -744,9 +755,35 @@ struct StreamEvents {
     }
 };
 
+// CUDA events around every routing and count kernel of a call (stats only).
+struct KernelTimes {
+    std::vector<cudaEvent_t> ev;
+    ~KernelTimes() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    tc_status mark(cudaStream_t s) {
+        cudaEvent_t e;
+        TC_CUDA_TRY(cudaEventCreate(&e));
+        ev.push_back(e);
+        TC_CUDA_TRY(cudaEventRecord(e, s));
+        return TC_OK;
+    }
+    // events are recorded as (route start, count start, count end) per part
+    void sum(float* route, float* count) const {
+        *route = *count = 0.f;
+        for (size_t k = 0; k + 2 < ev.size(); k += 3) {
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, ev[k], ev[k + 1]);
+            cudaEventElapsedTime(&b, ev[k + 1], ev[k + 2]);
+            *route += a;
+            *count += b;
+        }
+    }
+};
+
 tc_status surrogate_count(const int64_t* off, const int32_t* cols, int32_t n, int64_t m, const int32_t* cuts,
                           int32_t P, int32_t lo, int32_t hi, const tc_options& o, cudaStream_t s,
-                          std::vector<unsigned long long>* table) {
+                          std::vector<unsigned long long>* table, tc_surrogate_stats* stats) {
     Allocator al;
     al.alloc = o.alloc;
     al.release = o.release;
@@ -780,6 +817,7 @@ tc_status surrogate_count(const int64_t* off, const int32_t* cols, int32_t n, in
         TC_CUDA_TRY(cudaStreamSynchronize(s));
     }
     table->assign((size_t)P * P, 0ull);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
     if (m == 0 || lo == hi) return TC_OK;
     TC_TRY(device_cols(cols, m, &L));
     const bool direct = L.cols_device && ((uintptr_t)cols & 15u) == 0;
@@ -818,12 +856,15 @@ tc_status surrogate_count(const int64_t* off, const int32_t* cols, int32_t n, in
     const int cgrid = sms * std::max(per_sm, 1);
 
     StreamEvents ev;
+    KernelTimes kt;
+    int64_t copied = 0;
     auto copy_part = [&](int32_t j) -> tc_status {
         const int b = (j - lo) & 1;
         const int64_t e0 = oc[j] & ~(int64_t)3, len = oc[j + 1] - e0;
         if (j - lo >= 2) TC_CUDA_TRY(cudaStreamWaitEvent(ev.cs, ev.counted[b], 0));
         if (len > 0)
             TC_CUDA_TRY(cudaMemcpyAsync(res[b].ptr, cols + e0, (size_t)len * 4, cudaMemcpyDefault, ev.cs));
+        copied += 4 * std::max<int64_t>(len, 0);
         TC_CUDA_TRY(cudaEventRecord(ev.copied[b], ev.cs));
         return TC_OK;
     };
@@ -856,11 +897,16 @@ tc_status surrogate_count(const int64_t* off, const int32_t* cols, int32_t n, in
         a.nparts = P;
         a.j = j;
         a.table = tab.ptr;
+        a.counters = stats ? dev.ptr->counters : nullptr;
         a.st = st;
         TC_CUDA_TRY(cudaMemsetAsync(&dev.ptr->n_items, 0, 2 * sizeof(unsigned long long), s));
+        if (stats) TC_TRY(kt.mark(s));
         k_surrogate_route<<<ngrid, kRouteBlock, 0, s>>>(off_d, L.msrc, n, cuts_d.ptr, P, a.c_lo, a.c_hi, cur.ptr,
-                                                       nx.ptr, items.ptr, &dev.ptr->n_items, cap, st);
+                                                       nx.ptr, items.ptr, &dev.ptr->n_items, cap,
+                                                       stats ? &dev.ptr->counters[2] : nullptr, st);
+        if (stats) TC_TRY(kt.mark(s));
         k_surrogate_count<<<cgrid, kSWarps * 32, smem, s>>>(a);
+        if (stats) TC_TRY(kt.mark(s));
         note_launch(2);
         TC_CUDA_TRY(cudaGetLastError());
         if (!direct) {
@@ -873,7 +919,15 @@ tc_status surrogate_count(const int64_t* off, const int32_t* cols, int32_t n, in
         note_launch();
     }
     TC_CUDA_TRY(cudaMemcpyAsync(table->data(), tab.ptr, (size_t)P * P * 8, cudaMemcpyDeviceToHost, s));
-    return read_sdev(dev.ptr, s, &h);
+    const tc_status r = read_sdev(dev.ptr, s, &h);
+    if (stats) {
+        stats->staged = (int64_t)h.counters[0];
+        stats->streamed = (int64_t)h.counters[1];
+        stats->items = (int64_t)h.counters[2];
+        stats->copied_bytes = copied;
+        kt.sum(&stats->route_ms, &stats->count_ms);
+    }
+    return r;
 }
 
 tc_status surrogate_plan(const int64_t* off, const int32_t* cols, int32_t n, int64_t m, int fn, int32_t nparts,
@@ -959,7 +1013,7 @@ tc_status tc_surrogate_plan(const int64_t* off, const int32_t* cols, int32_t n, 
 
 tc_status tc_count_surrogate(const int64_t* off, const int32_t* cols, int32_t n, int64_t m, const int32_t* cuts,
                              int32_t nparts, int32_t part_lo, int32_t part_hi, const tc_options* opt,
-                             tc_stream_t stream, uint64_t* table, uint64_t* total) {
+                             tc_stream_t stream, uint64_t* table, uint64_t* total, tc_surrogate_stats* stats) {
     if (!off || !total || n < 0 || m < 0 || (m > 0 && !cols)) return TC_ERR_INVALID_ARG;
     if (n == INT32_MAX) return TC_ERR_UNSUPPORTED;
     TC_TRY(check_cuts(cuts, nparts, n));
@@ -969,7 +1023,8 @@ tc_status tc_count_surrogate(const int64_t* off, const int32_t* cols, int32_t n,
     if (opt) o = *opt;
     TC_TRY(check_options(o));
     std::vector<unsigned long long> tab;
-    tc_status r = surrogate_count(off, cols, n, m, cuts, nparts, part_lo, part_hi, o, (cudaStream_t)stream, &tab);
+    tc_status r = surrogate_count(off, cols, n, m, cuts, nparts, part_lo, part_hi, o, (cudaStream_t)stream, &tab,
+                                  stats);
     if (r != TC_OK) {
         (void)cudaGetLastError();
         return r;

@@ -64,7 +64,7 @@ def test_surrogate_argument_checks():
     def count(cuts, lo=0, hi=None, n=10, m=0):
         c = np.asarray(cuts, np.int32)
         return lib.tc_count_surrogate(o, None, n, m, c.ctypes.data_as(ctypes.c_void_p), len(c) - 1, lo,
-                                      len(c) - 1 if hi is None else hi, None, None, None, ctypes.byref(t))
+                                      len(c) - 1 if hi is None else hi, None, None, None, ctypes.byref(t), None)
 
     for cuts in ([1, 10], [0, 9], [0, 6, 5, 10], [0]):
         assert count(cuts) == _lib.TC_ERR_INVALID_ARG, cuts

@@ -272,3 +272,45 @@ def test_concurrent_calls_on_the_same_pageable_lists():
         t.join()
     assert not errors, errors
     assert ok == [True] * 12
+
+
+def _expected_stats(csr, cuts):
+    """The work tc_count_surrogate reports, from its definition on the oracle's lists: an item is a
+    run of at most 256 entries of one message in one part; each item stages its whole message; each
+    receiver entry u streams N_u once per staged piece of 512 message entries, trimmed to the piece's
+    [first, last] range when N_u has at least TC_TRIM_MIN_ENTRIES (16) entries."""
+    off, cols = csr.off, csr.cols
+    items = staged = streamed = 0
+    for j in range(len(cuts) - 1):
+        for v in range(csr.n):
+            X = cols[off[v]:off[v + 1]]
+            run = X[(X >= cuts[j]) & (X < cuts[j + 1])]
+            if not len(run):
+                continue
+            d = len(X)
+            k = -(-len(run) // 256)
+            items += k
+            staged += d * k
+            pieces = [(p, min(p + 512, d)) for p in range(0, d, 512)]
+            for u in run:
+                Nu = cols[off[u]:off[u + 1]]
+                for a, b in pieces:
+                    if len(Nu) >= _lib.TC_TRIM_MIN_ENTRIES:
+                        streamed += int(np.count_nonzero((Nu >= X[a]) & (Nu <= X[b - 1])))
+                    else:
+                        streamed += len(Nu)
+    return items, staged, streamed
+
+
+def test_work_counters():
+    small_dense = F.random_graph(700, 0.9, 3)  # lists up to ~630 entries: two pieces
+    for name, (n, s, d) in (("er_20k", GRAPHS["er_20k"]), ("small_dense", small_dense)):
+        csr = oracle.oriented_csr(oracle.simple_graph(n, s, d))
+        cuts = [0, n // 3, n // 2, n]
+        total, tab, st = tc.count_surrogate(csr.off, csr.cols, cuts, stats=True)
+        assert total == oracle.count(csr)
+        items, staged, streamed = _expected_stats(csr, cuts)
+        assert (st["items"], st["staged"], st["streamed"]) == (items, staged, streamed), name
+        assert st["copied_bytes"] == 4 * sum(int(csr.off[b]) - (int(csr.off[a]) & ~3)
+                                             for a, b in zip(cuts[:-1], cuts[1:]))
+        assert st["route_ms"] > 0 and st["count_ms"] > 0
