@@ -158,6 +158,17 @@ typedef struct tc_graph* tc_graph_t;
 tc_status tc_build(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
                    const tc_options* opt, tc_stream_t stream, tc_graph_t* out);
 
+/*
+ * tc_build for an edge list stored as interleaved pairs: edge i is (edges[2i], edges[2i+1]).
+ *   edges     host or device, 2 m int32; never modified.  A kernel splits the pairs into two
+ *             device arrays (page-locked host pairs are read in place, pageable ones copied
+ *             first), which then go through tc_build; they hold 8 m bytes more than tc_build's
+ *             peak while it runs, counted against opt->hbm_budget_bytes.
+ * Other arguments, results and errors as for tc_build.
+ */
+tc_status tc_build_pairs(const int32_t* edges, int64_t m, int32_t n, const tc_options* opt,
+                         tc_stream_t stream, tc_graph_t* out);
+
 /* Release a handle and its device memory (NULL-safe).  Waits for the stream of the
  * handle's last call; the handle must not be in use on any other stream. */
 void tc_free(tc_graph_t g);
@@ -177,6 +188,18 @@ tc_status tc_count(tc_graph_t g, tc_stream_t stream, uint64_t* total);
  * errors are reported by tc_graph_check.
  */
 tc_status tc_count_async(tc_graph_t g, tc_stream_t stream, uint64_t* total_dev);
+
+/*
+ * Count k graphs already built (each as tc_count), enqueued back to back on `stream`, with one
+ * synchronisation for all of them.  For many graphs not yet built, tc_batch_build packs them
+ * into disjoint unions that build and count in one pass each.
+ *   gs      host, k handles of the current device (a handle may repeat; none may be in use on
+ *           another stream).
+ *   totals  host, k uint64: totals[j] = T of gs[j].
+ * Errors: TC_ERR_INVALID_ARG (k < 0, NULL pointers), and the first error of any graph's count,
+ * in the order of gs.  Synchronises `stream`.
+ */
+tc_status tc_count_graphs(const tc_graph_t* gs, int32_t k, tc_stream_t stream, uint64_t* totals);
 
 /*
  * Count one part of the graph's tasks, for a count split over several GPUs (each holding a

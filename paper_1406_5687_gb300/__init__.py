@@ -17,7 +17,7 @@ from ._lib import (TC_COST_DEGREE, TC_COST_EDGE, TC_COST_MERGE, TC_COST_NEW, TC_
                    default_options)
 
 __all__ = ["Graph", "Batch", "autotune", "Server", "TcError", "default_options", "load", "version", "kernel_launches",
-           "count_surrogate", "surrogate_plan"]
+           "count_graphs", "count_surrogate", "surrogate_plan"]
 
 
 def load():
@@ -99,6 +99,21 @@ class Graph:
         rc = lib.tc_build(sp, dp, m, int(n), opt, _stream(stream), ctypes.byref(h))
         del keep
         _lib.check(rc, "tc_build")
+        return cls(h)
+
+    @classmethod
+    def build_pairs(cls, edges, n: int, options: _lib.Options | None = None, stream=None) -> "Graph":
+        """Build from interleaved pairs: `edges` is an (m, 2) int32 numpy array or torch tensor
+        (host or CUDA), edge i being (edges[i, 0], edges[i, 1])."""
+        lib = load()
+        ep, size, keep = _array_ptr(edges, "int32")
+        if size % 2:
+            raise ValueError("interleaved pairs need an even number of ids")
+        h = ctypes.c_void_p()
+        opt = ctypes.byref(options) if options is not None else None
+        rc = lib.tc_build_pairs(ep, size // 2, int(n), opt, _stream(stream), ctypes.byref(h))
+        del keep
+        _lib.check(rc, "tc_build_pairs")
         return cls(h)
 
     def free(self):
@@ -245,6 +260,15 @@ class Graph:
         cols = _view(c.value, mh, "<i4").clone()
         tasks = _view(t.value, 4 * T, "<i4").clone().view(-1, 4)
         return deg, off, cols, tasks
+
+
+def count_graphs(graphs, stream=None) -> list:
+    """Totals of several built graphs, counted back to back with one synchronisation."""
+    k = len(graphs)
+    hs = (ctypes.c_void_p * max(k, 1))(*[g.handle for g in graphs])
+    totals = (ctypes.c_uint64 * max(k, 1))()
+    _lib.check(load().tc_count_graphs(hs, k, _stream(stream), totals), "tc_count_graphs")
+    return [int(totals[j]) for j in range(k)]
 
 
 def _array_ptr(a, dtype_name: str):

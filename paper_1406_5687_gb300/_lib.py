@@ -118,6 +118,9 @@ SIGNATURES = {
     "tc_version": (ctypes.c_char_p, []),
     "tc_options_default": (None, [ctypes.POINTER(Options)]),
     "tc_build": (ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Options), P, ctypes.POINTER(P)]),
+    "tc_build_pairs": (ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Options), P,
+                                      ctypes.POINTER(P)]),
+    "tc_count_graphs": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int32, P, P]),
     "tc_free": (None, [P]),
     "tc_count": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_uint64)]),
     "tc_count_async": (ctypes.c_int, [P, P, P]),

@@ -1,4 +1,5 @@
 // api.cu -- the extern "C" entry points for single graphs declared in include/tc.h.
+#include <algorithm>
 #include <climits>
 #include <cstring>
 #include <new>
@@ -231,6 +232,59 @@ tc_status tc_build(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
     return TC_OK;
 }
 
+// Split interleaved pairs into the two device arrays tc_build takes.
+__global__ void k_split_pairs(const int32_t* __restrict__ pairs, int64_t m, int32_t* __restrict__ src,
+                              int32_t* __restrict__ dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        src[i] = pairs[2 * i];
+        dst[i] = pairs[2 * i + 1];
+    }
+}
+
+tc_status tc_build_pairs(const int32_t* edges, int64_t m, int32_t n, const tc_options* opt, tc_stream_t stream,
+                         tc_graph_t* out) {
+    if (!out) return TC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (m < 0 || n < 0) return TC_ERR_INVALID_ARG;
+    if (m > 0 && !edges) return TC_ERR_INVALID_ARG;
+    if (m == 0) return tc_build(nullptr, nullptr, 0, n, opt, stream, out);
+    tc_options o;
+    tc_options_default(&o);
+    if (opt) o = *opt;
+    TC_TRY(check_options(o));
+    cudaStream_t s = (cudaStream_t)stream;
+    retain_pool_memory();
+    Allocator al;
+    al.alloc = o.alloc;
+    al.release = o.release;
+    al.ctx = o.alloc_ctx;
+    tc_status st = TC_OK;
+    {
+        DevBuf<int32_t> sd, dd, staged;
+        TC_TRY(sd.alloc(&al, (size_t)m, s));
+        TC_TRY(dd.alloc(&al, (size_t)m, s));
+        const int32_t* pairs = is_device_pointer(edges) ? edges : (const int32_t*)pinned_device_view(edges);
+        if (!pairs) {  // pageable host pairs: one copy to the device first
+            TC_TRY(staged.alloc(&al, (size_t)(2 * m), s));
+            TC_CUDA_TRY(cudaMemcpyAsync(staged.ptr, edges, (size_t)m * 8, cudaMemcpyHostToDevice, s));
+            pairs = staged.ptr;
+        }
+        const int grid = (int)std::min<int64_t>(ceil_div(m, 256), (int64_t)num_sms() * 8);
+        k_split_pairs<<<grid, 256, 0, s>>>(pairs, m, sd.ptr, dd.ptr);
+        note_launch();
+        TC_CUDA_TRY(cudaGetLastError());
+        staged.release();
+        // the build's budget covers its own peak; the split arrays are held beside it
+        if (o.hbm_budget_bytes > 0) {
+            if (o.hbm_budget_bytes <= 8 * m) return TC_ERR_BUDGET;
+            o.hbm_budget_bytes -= 8 * m;
+        }
+        st = tc_build(sd.ptr, dd.ptr, m, n, &o, stream, out);
+        cudaStreamSynchronize(s);
+    }
+    return st;
+}
+
 void tc_free(tc_graph_t g) { free_graph(g); }
 
 tc_status tc_count(tc_graph_t g, tc_stream_t stream, uint64_t* total) {
@@ -248,6 +302,23 @@ tc_status tc_count_async(tc_graph_t g, tc_stream_t stream, uint64_t* total_dev) 
     if (!g || !total_dev) return TC_ERR_INVALID_ARG;
     g->last_stream = (cudaStream_t)stream;
     return count_enqueue(g, g->opt, (cudaStream_t)stream, (unsigned long long*)total_dev, nullptr, nullptr, nullptr);
+}
+
+tc_status tc_count_graphs(const tc_graph_t* gs, int32_t k, tc_stream_t stream, uint64_t* totals) {
+    if (k < 0 || (k > 0 && (!gs || !totals))) return TC_ERR_INVALID_ARG;
+    for (int32_t j = 0; j < k; ++j)
+        if (!gs[j]) return TC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int32_t j = 0; j < k; ++j) {
+        tc_graph* g = gs[j];
+        g->last_stream = s;
+        TC_TRY(count_enqueue(g, g->opt, s, g->work.result, nullptr, nullptr, nullptr));
+        // a repeated handle keeps its result word: take each total as soon as it is written
+        TC_CUDA_TRY(cudaMemcpyAsync(&totals[j], g->work.result, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    }
+    TC_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int32_t j = 0; j < k; ++j) TC_TRY(read_status(gs[j], s, nullptr));
+    return TC_OK;
 }
 
 tc_status tc_count_partition(tc_graph_t g, int32_t part, int32_t nparts, tc_stream_t stream, uint64_t* partial) {

@@ -48,6 +48,10 @@ def test_host_only_calls():
                 _lib.default_options(big_warps=32), _lib.default_options(static_percent=101)):
         assert lib.tc_build(None, None, 0, 10, ctypes.byref(bad), None, ctypes.byref(h)) == _lib.TC_ERR_INVALID_ARG
     assert lib.tc_count(None, None, None) == _lib.TC_ERR_INVALID_ARG
+    assert lib.tc_build_pairs(None, 5, 10, None, None, ctypes.byref(h)) == _lib.TC_ERR_INVALID_ARG
+    assert lib.tc_build_pairs(None, -1, 10, None, None, ctypes.byref(h)) == _lib.TC_ERR_INVALID_ARG
+    assert lib.tc_count_graphs(None, -1, None, None) == _lib.TC_ERR_INVALID_ARG
+    assert lib.tc_count_graphs(None, 2, None, None) == _lib.TC_ERR_INVALID_ARG
     lib.tc_free(None)
 
 
