@@ -108,20 +108,45 @@ __device__ __forceinline__ SView s_view(uint32_t* tbl, uint32_t reg) {
     return h;
 }
 
-// Linear probing; a region holds at most a quarter of its slots, so both loops end.
+// Linear probing from an even slot: the table is read as buckets of two slots, so one 8-byte
+// shared load covers the first two probes of a lookup.  A region holds at most a quarter of its
+// slots, so the loops end and most lookups end at their first bucket.
+__device__ __forceinline__ uint32_t s_start(const SView& h, uint32_t x) {
+    return ((x * kSHashMul) >> (h.shift + 1)) << 1;
+}
+
 __device__ __forceinline__ void s_insert(const SView& h, uint32_t x) {
-    uint32_t p = (x * kSHashMul) >> h.shift;
+    uint32_t p = s_start(h, x);
     while (atomicCAS(&h.tbl[p], kSEmpty, x) != kSEmpty) p = (p + 1u) & h.mask;
 }
 
-__device__ __forceinline__ bool s_find(const SView& h, uint32_t x) {
-    uint32_t p = (x * kSHashMul) >> h.shift;
+// The rest of a lookup whose first bucket held two other keys.
+__device__ __forceinline__ bool s_find_rest(const SView& h, uint32_t x, uint32_t p) {
     for (;;) {
         const uint32_t y = h.tbl[p];
         if (y == x) return true;
         if (y == kSEmpty) return false;
         p = (p + 1u) & h.mask;
     }
+}
+
+// Lookups of the four entries of a unit (those flagged in `ok`), their first buckets loaded
+// together; returns the hits.
+__device__ __forceinline__ uint32_t s_find4(const SView& h, const uint32_t (&x)[4], const bool (&ok)[4]) {
+    uint32_t p[4];
+    uint2 b[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) p[t] = s_start(h, x[t]);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) b[t] = *reinterpret_cast<const uint2*>(h.tbl + p[t]);
+    uint32_t hits = 0u;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        if (!ok[t]) continue;
+        if (b[t].x == x[t] || b[t].y == x[t]) ++hits;
+        else if (b[t].x != kSEmpty && b[t].y != kSEmpty && s_find_rest(h, x[t], (p[t] + 2u) & h.mask)) ++hits;
+    }
+    return hits;
 }
 
 // Both lists are ascending, so only the entries of the resident list r[ps, ps + len) inside
@@ -231,9 +256,10 @@ __device__ uint32_t s_batch(const SArgs& a, bool valid, uint32_t u, uint32_t reg
             if (!in[k]) continue;
             const SView hv = s_view(tbl, rg[k]);
             const uint32_t xs[4] = {(uint32_t)val[k].x, (uint32_t)val[k].y, (uint32_t)val[k].z, (uint32_t)val[k].w};
+            bool ok[4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t)
-                if (e0[k] + (uint32_t)t - lo[k] < ln[k] && s_find(hv, xs[t])) ++hits;
+            for (int t = 0; t < 4; ++t) ok[t] = e0[k] + (uint32_t)t - lo[k] < ln[k];
+            hits += s_find4(hv, xs, ok);
         }
     }
     return hits;
@@ -308,7 +334,9 @@ __device__ __forceinline__ unsigned long long s_receivers(const SArgs& a, uint32
     return acc;
 }
 
-__global__ void __launch_bounds__(kSWarps * 32) k_surrogate_count(SArgs a) {
+// Three blocks per SM: the register cap (80) that allows it costs a few spilled words, and beats
+// two blocks at 95 registers by a quarter.
+__global__ void __launch_bounds__(kSWarps * 32, 3) k_surrogate_count(SArgs a) {
     extern __shared__ uint32_t s_dyn[];
     uint32_t* const tbl = s_dyn + (threadIdx.x >> 5) * kSSlots;
     unsigned long long* const acc = reinterpret_cast<unsigned long long*>(s_dyn + kSWarps * kSSlots);
