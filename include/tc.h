@@ -404,6 +404,9 @@ tc_status tc_wait_selftest(int64_t spin_limit, tc_stream_t stream);
  * and threads, on the same lists.
  */
 #define TC_SURROGATE_MAX_PARTS 1024
+/* Messages longer than this are staged a piece of this many entries at a time, each resident list
+ * streamed once per piece (trimmed to the piece's [first, last] range). */
+#define TC_SURROGATE_PIECE 256
 typedef struct tc_surrogate_stats {
     int64_t items;         /* work items: runs of at most 256 entries of one message in one part */
     int64_t staged;        /* message entries staged into shared memory (X of Fig. 2) */

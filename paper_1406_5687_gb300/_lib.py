@@ -27,6 +27,7 @@ TC_INPUT_SANITIZE, TC_INPUT_STRICT = 0, 1
 TC_COUNT_STATIC_MAX_TASKS = 1 << 19  # include/tc.h
 TC_TRIM_MIN_ENTRIES = 16  # include/tc.h
 TC_SURROGATE_MAX_PARTS = 1024  # include/tc.h
+TC_SURROGATE_PIECE = 256  # include/tc.h
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)

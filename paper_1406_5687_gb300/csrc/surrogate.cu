@@ -41,11 +41,17 @@ namespace {
 
 constexpr uint32_t kSEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kSHashMul = 0x9E3779B1u;   // 2^32 / golden ratio (multiplicative hashing)
-constexpr int kSWarps = 8;                    // warps per block of the count kernel
-constexpr uint32_t kSSlots = 2048;            // hash slots of one warp's table
-constexpr uint32_t kSCap = kSSlots / 4;       // longest message staged whole (load <= 1/4)
+#ifndef TC_SURR_UNITS
+#define TC_SURR_UNITS 2
+#endif
+#ifndef TC_SURR_MIN_BLOCKS
+#define TC_SURR_MIN_BLOCKS 4
+#endif
+constexpr int kSWarps = 8;                          // warps per block of the count kernel
+constexpr uint32_t kSCap = TC_SURROGATE_PIECE;      // longest message staged whole; longer ones in pieces
+constexpr uint32_t kSSlots = 4 * kSCap;             // hash slots of one warp's table (load <= 1/4)
 constexpr uint32_t kItemU = 256;              // entries u of one work item
-constexpr int kSUnits = 4;                    // 16-byte units a lane loads per step
+constexpr int kSUnits = TC_SURR_UNITS;        // 16-byte units a lane loads per step
 constexpr uint32_t kSTrimMin = 16;            // shorter resident lists are streamed whole
 constexpr int kRouteBlock = 256;
 
@@ -334,9 +340,9 @@ __device__ __forceinline__ unsigned long long s_receivers(const SArgs& a, uint32
     return acc;
 }
 
-// Three blocks per SM: the register cap (80) that allows it costs a few spilled words, and beats
-// two blocks at 95 registers by a quarter.
-__global__ void __launch_bounds__(kSWarps * 32, 3) k_surrogate_count(SArgs a) {
+// Four blocks of 8 warps per SM (64 registers, 4 KB of table per warp): the kernel is bound by
+// its probe stream, and the extra warps hide its latency better than the registers they cost.
+__global__ void __launch_bounds__(kSWarps * 32, TC_SURR_MIN_BLOCKS) k_surrogate_count(SArgs a) {
     extern __shared__ uint32_t s_dyn[];
     uint32_t* const tbl = s_dyn + (threadIdx.x >> 5) * kSSlots;
     unsigned long long* const acc = reinterpret_cast<unsigned long long*>(s_dyn + kSWarps * kSSlots);

@@ -43,8 +43,8 @@ def _graphs():
     n = 200000
     s, d = graphgen.chung_lu(n, 2.1, 20.0, 8000.0, 2_000_000, 23)
     out["cl_200k"] = (n, s, d)
-    # dense: lists of up to ~800 entries (longer than one staged piece of 512), runs of more
-    # than 256 entries inside one part (several work items per message)
+    # dense: lists of up to ~800 entries (several staged pieces), runs of more than 256 entries
+    # inside one part (several work items per message)
     out["dense_1400"] = F.random_graph(1400, 0.6, 7)
     return out
 
@@ -124,7 +124,7 @@ def test_part_ranges_add_up(name):
 
 def test_dense_lists_exercise_pieces_and_split_items():
     csr = CSR["dense_1400"]
-    assert csr.dhat.max() > 512  # longer than one staged piece
+    assert csr.dhat.max() > 2 * _lib.TC_SURROGATE_PIECE  # three staged pieces
     cuts = [0, 700, 1400]
     runs = [np.count_nonzero((csr.cols[csr.off[v]:csr.off[v + 1]] >= 700)) for v in range(csr.n)]
     assert max(runs) > 256  # one message split into several work items
@@ -277,8 +277,8 @@ def test_concurrent_calls_on_the_same_pageable_lists():
 def _expected_stats(csr, cuts):
     """The work tc_count_surrogate reports, from its definition on the oracle's lists: an item is a
     run of at most 256 entries of one message in one part; each item stages its whole message; each
-    receiver entry u streams N_u once per staged piece of 512 message entries, trimmed to the piece's
-    [first, last] range when N_u has at least TC_TRIM_MIN_ENTRIES (16) entries."""
+    receiver entry u streams N_u once per staged piece of TC_SURROGATE_PIECE message entries, trimmed
+    to the piece's [first, last] range when N_u has at least TC_TRIM_MIN_ENTRIES (16) entries."""
     off, cols = csr.off, csr.cols
     items = staged = streamed = 0
     for j in range(len(cuts) - 1):
@@ -291,7 +291,8 @@ def _expected_stats(csr, cuts):
             k = -(-len(run) // 256)
             items += k
             staged += d * k
-            pieces = [(p, min(p + 512, d)) for p in range(0, d, 512)]
+            L = _lib.TC_SURROGATE_PIECE
+            pieces = [(p, min(p + L, d)) for p in range(0, d, L)]
             for u in run:
                 Nu = cols[off[u]:off[u + 1]]
                 for a, b in pieces:
@@ -303,7 +304,7 @@ def _expected_stats(csr, cuts):
 
 
 def test_work_counters():
-    small_dense = F.random_graph(700, 0.9, 3)  # lists up to ~630 entries: two pieces
+    small_dense = F.random_graph(700, 0.9, 3)  # lists up to ~630 entries: three pieces
     for name, (n, s, d) in (("er_20k", GRAPHS["er_20k"]), ("small_dense", small_dense)):
         csr = oracle.oriented_csr(oracle.simple_graph(n, s, d))
         cuts = [0, n // 3, n // 2, n]
