@@ -65,6 +65,10 @@ def parse_args():
     p.add_argument("--partitioned", action="store_true",
                    help="one graph split over the ranks: every rank builds it and counts its cost-balanced "
                         "part of the tasks; the partial counts are summed (strong scaling)")
+    p.add_argument("--partition-mode", default="tasks", choices=["tasks", "surrogate"],
+                   help="with --partitioned: split the cost-ordered tasks of a replica (tasks), or give each "
+                        "rank its receiving parts of Sec. IV's non-overlapping partition of the lists, read from "
+                        "page-locked host memory (surrogate)")
     p.add_argument("--ablation", action="store_true",
                    help="count the workload under every cost model and static share of Eq. 1 and print one "
                         "JSON line per setting (kernel times and per-worker idle spread)")
@@ -762,6 +766,80 @@ def run_serve_only(args, rank, world, local):
     return 0
 
 
+def surrogate_part_range(world, rank, nparts):
+    """Receiving parts [lo, hi) of rank `rank` when `nparts` parts are shared by `world` ranks:
+    contiguous ranges whose sizes differ by at most one."""
+    return rank * nparts // world, (rank + 1) * nparts // world
+
+
+def run_partitioned_surrogate(args, rank, world, local):
+    """One graph's N+ lists, held in page-locked host memory by every rank, counted by all ranks
+    over Sec. IV's non-overlapping partition: equal-work cuts (Sec. IV-F cost) into one part per
+    rank, each rank counting the messages its part receives (tc_count_surrogate with its part
+    range); one uint64 sum over the ranks gives T.  Strong scaling."""
+    import torch
+    import paper_1406_5687_gb300 as tc
+    from graphgen import workloads as W
+    torch.cuda.set_device(local)
+    pg = init_replicas(world)
+    spec = W.SINGLE[args.workload]
+    s, d = spec.edges()
+    s_dev, d_dev = torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda()
+    del s, d
+    stream = torch.cuda.current_stream()
+    g0 = tc.Graph.build(s_dev, d_dev, spec.n)
+    T_ref, m_hat = g0.count(stream), g0.info()["m_hat"]
+    _, off, cols, _ = g0.csr()
+    g0.free()
+    del s_dev, d_dev
+    off_h, cols_h = off.cpu().pin_memory(), cols.cpu().pin_memory()
+    del off, cols
+    torch.cuda.empty_cache()
+    cuts = tc.surrogate_plan(off_h, cols_h, nparts=world, fn=tc.TC_FN_NEW)
+    lo, hi = surrogate_part_range(world, rank, len(cuts) - 1)
+
+    def step():
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        part, _tab = tc.count_surrogate(off_h, cols_h, cuts, part_lo=lo, part_hi=hi, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), part
+
+    for _ in range(args.warmup):
+        step()
+    if pg:
+        pg.barrier()
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get(
+        "CUDA_VISIBLE_DEVICES") else str(local)
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    l0 = tc.kernel_launches()
+    steps = [step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    launches = tc.kernel_launches() - l0
+    clk = clocks.stop()
+    total_ms = max_over_ranks(pg, sum(x[0] for x in steps))
+    T = sum_over_ranks(pg, steps[-1][1])
+    if pg:
+        pg.barrier()
+    if T != T_ref:
+        raise RuntimeError(f"partial counts sum to {T}, not {T_ref}")
+    if rank == 0:
+        line = {"metric": METRIC, "value": replica_throughput(1, args.steps, m_hat, total_ms), "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD_TEXT[args.workload], "m_hat": m_hat, "triangles": T,
+                           "l2": "inputs larger than L2", "lists": "page-locked host memory",
+                           "parallelism": f"non-overlapping partition, one equal-work part per rank, {world} ranks"},
+                "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
 def run_partitioned(args, rank, world, local):
     """One graph counted by all ranks: each builds it (a replica) and counts part `rank` of
     `world` cost-balanced parts of its tasks (tc_count_partition); one uint64 sum over the ranks
@@ -878,6 +956,8 @@ def run_gpu(args, rank, world, local):
     if args.ablation:
         return run_ablation(args, local) if rank == 0 else 0
     if args.partitioned:
+        if args.partition_mode == "surrogate":
+            return run_partitioned_surrogate(args, rank, world, local)
         return run_partitioned(args, rank, world, local)
 
     if args.workload == "batch":

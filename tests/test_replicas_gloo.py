@@ -65,3 +65,57 @@ def test_single_process_needs_no_group():
     assert bench.max_over_ranks(None, 12.5) == 12.5
     assert bench.replica_throughput(1, 4, 10, 20.0) == pytest.approx(2000.0)
     assert bench.sum_over_ranks(None, 7) == 7
+
+
+def _surrogate_worker(rank, world, port, out):
+    """A rank of the partitioned non-overlapping count: its receiving parts of the table, with
+    the oracle standing in for the GPU count, summed over the ranks."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    import graphgen
+    import oracle
+    n = 3000
+    s, d = graphgen.chung_lu(n, 2.1, 12.0, 600.0, 24_000, 9)
+    csr = oracle.oriented_csr(oracle.simple_graph(n, s, d))
+    cuts = oracle.balanced_cuts(oracle.vertex_cost(csr, oracle.COST_NEW), 2 * world + 1)
+    lo, hi = bench.surrogate_part_range(world, rank, len(cuts) - 1)
+    part = int(oracle.count_parts(csr, cuts)[:, lo:hi].sum())
+    r, w, _ = bench.dist_env()
+    pg = bench.init_replicas(w)
+    total = bench.sum_over_ranks(pg, part)
+    pg.barrier()
+    out.put((r, lo, hi, total, oracle.count(csr)))
+    pg.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_partition_ranges_of_the_ranks_add_up(world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_surrogate_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    # the ranks' ranges tile [0, P) in order, and the partial counts sum to T
+    assert res[0][1] == 0 and res[-1][2] == 2 * world + 1
+    assert all(a[2] == b[1] for a, b in zip(res, res[1:]))
+    for _, _, _, total, T in res:
+        assert total == T
+
+
+def test_part_ranges_cover_every_part_once():
+    sys.path.insert(0, ROOT)
+    import bench
+    for world in range(1, 9):
+        for P in range(0, 40):
+            got = [bench.surrogate_part_range(world, r, P) for r in range(world)]
+            assert got[0][0] == 0 and got[-1][1] == P
+            assert all(a[1] == b[0] for a, b in zip(got, got[1:]))
+            assert all(0 <= hi - lo - P // world <= 1 for lo, hi in got)
