@@ -88,3 +88,26 @@ def test_surrogate_argument_checks():
                                  ctypes.byref(P)) == _lib.TC_ERR_INVALID_ARG
     for fn in (-1, _lib.TC_FN_LIST + 1):
         assert lib.tc_surrogate_plan(o, None, 10, 0, fn, 2, 0, 7, None, cp, ctypes.byref(P)) == _lib.TC_ERR_INVALID_ARG
+
+
+def test_header_compiles_as_c_and_links():
+    """include/tc.h as plain C11 against the shared library, with the calls that need no device."""
+    import shutil
+    import subprocess
+    import tempfile
+    from paper_1406_5687_gb300 import _lib
+    _lib.load()
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc is not installed")
+    libdir = os.path.dirname(_lib.library_path())
+    with tempfile.TemporaryDirectory() as tmp:
+        exe = os.path.join(tmp, "abi_from_c")
+        cmd = [gcc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+               os.path.join(ROOT, "tests", "native", "abi_from_c.c"), "-L", libdir, "-ltcgb300",
+               "-Wl,-rpath," + libdir, "-o", exe]
+        build = subprocess.run(cmd, capture_output=True, text=True)
+        assert build.returncode == 0, build.stderr
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+        assert r.returncode == 0, r.stdout + r.stderr
+        assert "abi from C: ok" in r.stdout
