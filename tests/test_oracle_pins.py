@@ -383,3 +383,23 @@ def test_balanced_cuts_closed_forms():
     assert oracle.balanced_cuts(big, 4).tolist() == [0, 1, 2, 3, 4]
     with pytest.raises(oracle.OracleError):
         oracle.balanced_cuts(np.ones(3, np.uint64), 0)
+
+
+def test_partition_table_closed_form_on_complete_graph():
+    """K_n: all degrees tie, so the order is by id and triangle {x < y < z} is counted by the part
+    of its middle vertex y for the part of x.  Entry (i, j) is the number of (x, y, z) with
+    x < y < z, x in V_i and y in V_j: the sum over y in V_j of |{x in V_i : x < y}| (n - 1 - y)."""
+    from graphgen import families as F
+    n, s, d = F.complete(40)
+    csr = oracle.oriented_csr(oracle.simple_graph(n, s, d))
+    for cuts in ([0, 40], [0, 7, 7, 20, 33, 40], list(range(0, 41, 5)), [0, 1, 39, 40]):
+        P = len(cuts) - 1
+        want = np.zeros((P, P), np.int64)
+        for i in range(P):
+            for j in range(P):
+                for y in range(cuts[j], cuts[j + 1]):
+                    below = max(0, min(cuts[i + 1], y) - cuts[i])
+                    want[i, j] += below * (n - 1 - y)
+        got = oracle.count_parts(csr, cuts).astype(np.int64)
+        assert np.array_equal(got, want), cuts
+        assert int(want.sum()) == n * (n - 1) * (n - 2) // 6
