@@ -40,7 +40,7 @@ WORKLOAD_TEXT = {
     "cl_twitter": "chung-lu n=41,650,000 exponent 2.1 mean degree 115 w0=3e6, 2.4e9 edge draws, seed 5 "
                   "(the size of the paper's Twitter graph)",
 }
-# input pairs of the same workload the oracle counts per CPU-baseline run (about 10-30 s)
+# input pairs of the prefix the CPU baseline also times on one core, end to end
 CPU_SAMPLE_PAIRS = {"cl": 32_000_000, "ba": 16_000_000, "er": 100_000, "cl_small": 8_000_000, "cl_twitter": 32_000_000}
 # input pairs per step of the reference (oracle) arm, so that --steps K --warmup W ends in minutes
 REF_SAMPLE_PAIRS = {"cl": 4_000_000, "ba": 2_000_000, "er": 100_000, "cl_small": 2_000_000, "cl_twitter": 4_000_000}
@@ -73,12 +73,11 @@ def parse_args():
                    help="count the workload under every cost model and static share of Eq. 1 and print one "
                         "JSON line per setting (kernel times and per-worker idle spread)")
     p.add_argument("--serve-requests", type=int, default=0,
-                   help="requests of the serving window (default: 256 as a leg of a single-graph run, 2000 "
-                        "with --workload serve)")
+                   help="requests of the serving window (default 2000)")
     p.add_argument("--serve-slots", type=int, default=4, help="slot threads of the server")
     p.add_argument("--serve-group-edges", type=int, default=0, help="input edges one slot takes at once (0: default)")
     p.add_argument("--serve-pool", type=int, default=0,
-                   help="pre-generated graphs the requests cycle through (default 32, or 256 with --workload serve)")
+                   help="pre-generated graphs the requests cycle through (default 256)")
     p.add_argument("--no-surrogate", action="store_true",
                    help="skip the leg that counts the lists over a non-overlapping partition (Sec. IV) from "
                         "page-locked host memory")
@@ -86,8 +85,7 @@ def parse_args():
                    help="the part-size bound of that leg, as a fraction of the lists (default 4: each part "
                         "holds at most a quarter of them)")
     p.add_argument("--batch-graphs", type=int, default=0,
-                   help="graphs of the batched workload (default: 512 as a leg of a single-graph run, "
-                        "4096 with --workload batch)")
+                   help="graphs of the batched workload (default 4096)")
     return p.parse_args()
 
 
@@ -273,37 +271,56 @@ def algorithmic_bytes(g, opt):
             "untrimmed_big_entries": int(info["sum_stream"]) - int(streamed[0])}
 
 
-def cpu_baseline(workload, pairs, threads=1):
-    """The oracle as it stands (simple graph, Fig. 1 lists, Fig. 1 count) on the first
-    `pairs` input pairs of the workload, timed on the host."""
+def cpu_baseline(workload, sample_pairs, single_thread_budget_s=60.0):
+    """The oracle as it stands (simple graph, Fig. 1 lists, Fig. 1 count) on the whole benched
+    graph, timed on the host: the simple graph and the lists as the oracle builds them (one
+    thread), then the count loop with the oracle's OpenMP option on every host core.  The value
+    is m_hat over that end-to-end time.  Beside it: the count loop alone on all cores and, when
+    the all-core time says it fits `single_thread_budget_s`, on one core (the same CSR); and the
+    older single-thread figure on the first `sample_pairs` input pairs."""
     import oracle
     from graphgen import workloads as W
     spec = W.SINGLE[workload]
-    if spec.family == "cl":
-        import dataclasses
-        s, d = dataclasses.replace(spec, draws=min(pairs, spec.draws)).edges()
-    else:
-        s, d = spec.edges()
-        s, d = s[:pairs], d[:pairs]
+    cores = os.cpu_count() or 1
+    s, d = spec.edges()
     t0 = time.perf_counter()
     csr = oracle.oriented_csr(oracle.simple_graph(spec.n, s, d))
     t1 = time.perf_counter()
-    T = oracle.count(csr, threads=threads)
-    dt = time.perf_counter() - t0
-    count_s = time.perf_counter() - t1
-    # the oracle's own OpenMP option of the count loop (dynamic schedule, every host core)
-    cores = os.cpu_count() or 1
+    T = oracle.count(csr, threads=cores)
     t2 = time.perf_counter()
-    T2 = oracle.count(csr, threads=cores)
-    omp_s = time.perf_counter() - t2
-    if T2 != T:
-        raise RuntimeError("oracle count differs between thread counts")
-    return {"value": csr.m_hat / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {len(s):,} input pairs of the workload ({csr.m_hat:,} distinct edges, {T:,} triangles), "
-                      f"oracle end to end (simple graph, Fig. 1 lists, Fig. 1 count), {dt:.2f} s",
-            "count_only": {"value": csr.m_hat / count_s, "cores": threads, "seconds": count_s},
-            "count_only_all_cores": {"value": csr.m_hat / omp_s, "cores": cores, "seconds": omp_s,
-                                     "note": "the same count loop with OpenMP over every host core"}}
+    build_s, count_s = t1 - t0, t2 - t1
+    out = {"value": csr.m_hat / (t2 - t0), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"the whole benched graph ({len(s):,} input pairs, {csr.m_hat:,} distinct edges, {T:,} triangles): "
+                     f"the oracle's simple graph and Fig. 1 lists on one thread ({build_s:.2f} s), then its Fig. 1 "
+                     f"count loop with OpenMP over all {cores} host cores ({count_s:.2f} s)",
+           "seconds": t2 - t0, "build_seconds": build_s, "triangles": T,
+           "count_only_all_cores": {"value": csr.m_hat / count_s, "cores": cores, "seconds": count_s}}
+    if count_s * cores <= single_thread_budget_s:
+        t3 = time.perf_counter()
+        T1 = oracle.count(csr, threads=1)
+        c1 = time.perf_counter() - t3
+        if T1 != T:
+            raise RuntimeError("oracle count differs between thread counts")
+        out["count_only_one_core"] = {"value": csr.m_hat / c1, "cores": 1, "seconds": c1}
+    else:
+        out["count_only_one_core"] = {"value": None, "cores": 1,
+                                      "note": f"not run: about {count_s * cores:.0f} s expected (all-core time x "
+                                              f"{cores} cores), over the bench's {single_thread_budget_s:.0f} s bound"}
+    del csr, s, d
+    # the single-thread end-to-end figure on a prefix of the same workload
+    if spec.family == "cl":
+        import dataclasses
+        s, d = dataclasses.replace(spec, draws=min(sample_pairs, spec.draws)).edges()
+    else:
+        s, d = spec.edges()
+        s, d = s[:sample_pairs], d[:sample_pairs]
+    t4 = time.perf_counter()
+    c2 = oracle.oriented_csr(oracle.simple_graph(spec.n, s, d))
+    oracle.count(c2, threads=1)
+    dt = time.perf_counter() - t4
+    out["one_core_prefix"] = {"value": c2.m_hat / dt, "cores": 1, "seconds": dt,
+                              "sample": f"first {len(s):,} input pairs ({c2.m_hat:,} distinct edges), end to end"}
+    return out
 
 
 # --------------------------------------------------------------------------- batched and plain
@@ -1097,14 +1114,14 @@ def run_gpu(args, rank, world, local):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, CPU_SAMPLE_PAIRS[args.workload])
+        cpu["gpu_same_graph"] = {"step_ms": total_ms / args.steps, "build_ms": build_ms, "count_ms": count_ms}
 
     batch = None
     if rank == 0 and not args.no_batch:
-        batch = batch_leg(args.batch_graphs or 512, max(2, min(args.steps, 3)), args.warmup,
-                          pack_edges=args.pack_edges)
+        batch = batch_leg(args.batch_graphs or 4096, 2, 1, pack_edges=args.pack_edges)
     serve = None
     if rank == 0 and not args.no_serve:
-        serve = serve_leg(args.serve_requests or 256, args.serve_pool or 32, args.serve_slots, args.serve_group_edges)
+        serve = serve_leg(args.serve_requests or 2000, args.serve_pool or 256, args.serve_slots, args.serve_group_edges)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

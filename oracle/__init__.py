@@ -27,7 +27,6 @@ _lock = threading.Lock()
 
 OK, ERR_INVALID_ARG, ERR_VERTEX_RANGE, ERR_OOM = 0, 1, 2, 3
 COST_ONE, COST_DEGREE, COST_PATRIC, COST_NEW = 0, 1, 2, 3
-MODEL_EDGE, MODEL_MERGE, MODEL_VERTEX = 0, 1, 2
 
 
 class OracleError(RuntimeError):
@@ -72,11 +71,6 @@ def _load():
             L.or_balanced_cuts.restype = ctypes.c_int
             L.or_vertex_cost.argtypes = [ctypes.c_int, i32, P, P, P, P]
             L.or_vertex_cost.restype = ctypes.c_int
-            L.or_tasks.argtypes = [i32, P, P, i64, P, P, P, ctypes.POINTER(i64)]
-            L.or_tasks.restype = i64
-            L.or_task_costs.argtypes = [ctypes.c_int, ctypes.c_int, i32, i64, i32, i32, i32, P, P, P,
-                                        i64, P, P, P]
-            L.or_task_costs.restype = ctypes.c_int
             L.or_schedule.argtypes = [i64, P, i64, u64, P, P, i64]
             L.or_schedule.restype = i64
             _lib = L
@@ -196,41 +190,6 @@ def vertex_cost(csr: OrientedCSR, fn: int) -> np.ndarray:
     if rc != OK:
         raise OracleError(rc)
     return f[:csr.n]
-
-
-def tasks(csr: OrientedCSR, small_max: int = 1 << 40, with_split: bool = False, with_pos: bool = False):
-    """Owner-grouped tasks: (owner int32[T], partner int32[T]) sorted by (class, owner, position of
-    the oriented edge in csr.cols), small class first (owner list of at most small_max entries).
-    With with_split, also the number of small tasks; with with_pos, also the positions."""
-    L = _load()
-    cap = max(csr.m_hat, 1)
-    o = np.empty(cap, np.int32)
-    p = np.empty(cap, np.int32)
-    pos = np.empty(cap, np.int64)
-    ns = ctypes.c_int64()
-    t = L.or_tasks(csr.n, _p(csr.off), _p(csr.cols), int(small_max), _p(o), _p(p), _p(pos), ctypes.byref(ns))
-    if t < 0:
-        raise OracleError(ERR_OOM)
-    out = [o[:t].copy(), p[:t].copy()]
-    if with_split:
-        out.append(int(ns.value))
-    if with_pos:
-        out.append(pos[:t].copy())
-    return tuple(out)
-
-
-def task_costs(csr: OrientedCSR, owner, partner, model=MODEL_EDGE, fn=COST_DEGREE,
-               piece=1024, c_task=4, c_owner=32, small_max: int = 0) -> np.ndarray:
-    L = _load()
-    T = len(owner)
-    cost = np.zeros(max(T, 1), np.uint64)
-    owner = np.ascontiguousarray(owner, np.int32)
-    partner = np.ascontiguousarray(partner, np.int32)
-    rc = L.or_task_costs(int(model), int(fn), int(piece), int(small_max), int(c_task), int(c_owner), csr.n,
-                         _p(csr.deg), _p(csr.off), _p(csr.cols), T, _p(owner), _p(partner), _p(cost))
-    if rc != OK:
-        raise OracleError(rc)
-    return cost[:T]
 
 
 def schedule(cost, workers: int, min_chunk: int):

@@ -41,14 +41,13 @@
  *                     costs each come to about 1/P of the total: cut k is the
  *                     first vertex q whose cost prefix f(0) + ... + f(q-1)
  *                     reaches k/P of the total (cut 0 = 0, cut P = n).
- *   or_tasks,         The GPU's work decomposition, restated from its
- *   or_task_costs,    definition: each oriented edge becomes one task owned by
- *   or_schedule       the endpoint with the longer list, in a small or a big
- *                     class by the owner's list length; task costs; the chunk
- *                     table of the dynamic load balancing scheme -- the first
- *                     half of the total cost split into W equal initial tasks
- *                     (Sec. V-B, Eq. 1) and the rest handed out in chunks of
- *                     remaining/W (Eq. 2) with a floor.
+ *   or_schedule       Sec. V-B: the chunk table of the dynamic load balancing
+ *                     scheme over a sequence of task costs -- the first half
+ *                     of the total cost split into W equal initial tasks (Eq. 1)
+ *                     and the rest handed out in chunks of remaining/W (Eq. 2)
+ *                     with a floor.  Which tasks there are, and what each costs,
+ *                     is the caller's input: the paper's per-vertex costs come
+ *                     from or_vertex_cost.
  *
  * Parity of every function is pinned by the tests against brute force,
  * trace(A^3)/6, closed forms and invariants; none is "parity unpinned".
@@ -74,11 +73,6 @@ typedef struct {
 
 static int cmp_i32(const void* a, const void* b) {
     int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
-    return (x > y) - (x < y);
-}
-
-static int cmp_u64(const void* a, const void* b) {
-    uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
     return (x > y) - (x < y);
 }
 
@@ -320,99 +314,6 @@ int or_vertex_cost(int fn, int32_t n, const int32_t* deg, const int64_t* off, co
             return OR_ERR_INVALID_ARG;
         }
     }
-    return OR_OK;
-}
-
-/*
- * Work decomposition of the GPU path, from its definition: for each oriented edge
- * (v, u) the owner is the endpoint with the longer list (v when dh_v >= dh_u) and
- * the partner is the other one; the triangle count of the edge is
- * |N_owner intersect N_partner|.  Tasks whose partner list is empty are dropped
- * (they count nothing).  A task is "small" when its owner's list has at most
- * small_max entries, else "big".  Tasks are sorted by (class, owner, position of
- * the oriented edge in cols): all small tasks first.  owner/partner/pos need
- * capacity m_hat (pos may be NULL); *n_small receives the number of small tasks.
- * Returns the number of tasks, or -1 on OOM or more than 2^32 edges.
- */
-int64_t or_tasks(int32_t n, const int64_t* off, const int32_t* cols, int64_t small_max, int32_t* owner,
-                 int32_t* partner, int64_t* pos, int64_t* n_small) {
-    int64_t mh = off[n];
-    if (mh >= ((int64_t)1 << 32)) return -1;
-    uint64_t* key = (uint64_t*)malloc((size_t)(mh > 0 ? mh : 1) * sizeof(uint64_t));
-    int32_t* row = (int32_t*)malloc((size_t)(mh > 0 ? mh : 1) * sizeof(int32_t));
-    if (!key || !row) { free(key); free(row); return -1; }
-    int64_t t = 0, ns = 0;
-    for (int32_t v = 0; v < n; ++v) {
-        int64_t dv = off[v + 1] - off[v];
-        for (int64_t i = off[v]; i < off[v + 1]; ++i) {
-            row[i] = v;
-            int32_t u = cols[i];
-            int64_t du = off[u + 1] - off[u];
-            int32_t o = dv >= du ? v : u;
-            int32_t p = dv >= du ? u : v;
-            if (off[p + 1] - off[p] == 0) continue;
-            uint64_t big = (off[o + 1] - off[o]) > small_max ? 1u : 0u;
-            if (!big) ++ns;
-            key[t++] = (big << 63) | ((uint64_t)(uint32_t)o << 32) | (uint64_t)i;
-        }
-    }
-    qsort(key, (size_t)t, sizeof(uint64_t), cmp_u64);
-    for (int64_t k = 0; k < t; ++k) {
-        int64_t i = (int64_t)(key[k] & 0xFFFFFFFFu);
-        int32_t o = (int32_t)((key[k] >> 32) & 0x7FFFFFFFu);
-        owner[k] = o;
-        partner[k] = row[i] == o ? cols[i] : row[i];
-        if (pos) pos[k] = i;
-    }
-    free(key);
-    free(row);
-    *n_small = ns;
-    return t;
-}
-
-enum { OR_MODEL_EDGE = 0, OR_MODEL_MERGE = 1, OR_MODEL_VERTEX = 2 };
-
-/*
- * Cost of each task.
- *   EDGE   (the GPU's own model of its hash-probe work): the owner's list is
- *          staged in pieces of at most `piece` entries (one piece when it has at
- *          most small_max entries), each partner list is streamed once per piece:
- *          cost = pieces(owner) * (dh_partner + c_task); the owner's last task also
- *          carries the staging cost dh_owner + c_owner.
- *   MERGE  the paper's per-edge merge cost dh_v + dh_u (Sec. III-A).
- *   VERTEX the paper's per-vertex cost f (from or_vertex_cost with function fn),
- *          put on the owner's last task so that a chunk never splits an owner:
- *          the atomic task <v,1> of Sec. V-A.
- */
-int or_task_costs(int model, int fn, int32_t piece, int64_t small_max, int32_t c_task, int32_t c_owner,
-                  int32_t n, const int32_t* deg, const int64_t* off, const int32_t* cols,
-                  int64_t T, const int32_t* owner, const int32_t* partner, uint64_t* cost) {
-    uint64_t* f = NULL;
-    if (model == OR_MODEL_VERTEX) {
-        f = (uint64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(uint64_t));
-        if (!f) return OR_ERR_OOM;
-        int rc = or_vertex_cost(fn, n, deg, off, cols, f);
-        if (rc != OR_OK) { free(f); return rc; }
-    } else if (model != OR_MODEL_EDGE && model != OR_MODEL_MERGE) {
-        return OR_ERR_INVALID_ARG;
-    }
-    if (model == OR_MODEL_EDGE && piece < 1) return OR_ERR_INVALID_ARG;
-    for (int64_t t = 0; t < T; ++t) {
-        int32_t o = owner[t], p = partner[t];
-        uint64_t dho = (uint64_t)(off[o + 1] - off[o]);
-        uint64_t dhp = (uint64_t)(off[p + 1] - off[p]);
-        int last = (t + 1 == T) || owner[t + 1] != o;
-        if (model == OR_MODEL_EDGE) {
-            uint64_t pieces = dho <= (uint64_t)small_max ? 1 : (dho + (uint64_t)piece - 1) / (uint64_t)piece;
-            cost[t] = pieces * (dhp + (uint64_t)c_task);
-            if (last) cost[t] += dho + (uint64_t)c_owner;
-        } else if (model == OR_MODEL_MERGE) {
-            cost[t] = dho + dhp;
-        } else {
-            cost[t] = last ? f[o] : 0;
-        }
-    }
-    free(f);
     return OR_OK;
 }
 

@@ -1162,7 +1162,7 @@ namespace tcg {
 
 constexpr long long kStaticMaxTasks = TC_COUNT_STATIC_MAX_TASKS;  // a 4 MiB cost prefix
 constexpr long long kStaticPrefixWords = kStaticMaxTasks + 1;
-constexpr long long kStaticScanWords = 512;  // scan_scratch_words(kStaticMaxTasks) = 257
+constexpr long long kStaticScanWords = 512;  // the scan's tile sums; each call checks its need against this
 constexpr long long kStaticSchedWords = (2 * sizeof(Sched) + 7) / 8;
 constexpr long long kStaticWords = kStaticPrefixWords + kStaticScanWords + kStaticSchedWords;
 
@@ -1191,7 +1191,8 @@ static tc_status count_enqueue_static(tc_graph* g, cudaStream_t s, unsigned long
     if (opt.cost_model != TC_COST_EDGE && opt.cost_model != TC_COST_MERGE) return TC_ERR_INVALID_ARG;
     const long long T = g->tasks, Ts = g->tasks_small;
     if (T > kStaticMaxTasks) return TC_ERR_UNSUPPORTED;
-    static_assert(kStaticScanWords >= 257, "scan scratch for kStaticMaxTasks tasks");
+    // the scan's scratch must fit its region, or it would run into the schedule records
+    if (scan_scratch_words(T) > kStaticScanWords) return TC_ERR_UNSUPPORTED;
     unsigned long long* base = nullptr;
     TC_TRY(static_scratch(&base));
     uint64_t* prefix = (uint64_t*)base;

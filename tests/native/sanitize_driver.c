@@ -28,11 +28,6 @@ int or_count_parts(int32_t n, const int64_t* off, const int32_t* cols, int32_t n
                    uint64_t* out);
 int or_balanced_cuts(int32_t n, const uint64_t* f, int32_t P, int32_t* cuts);
 int or_vertex_cost(int fn, int32_t n, const int32_t* deg, const int64_t* off, const int32_t* cols, uint64_t* f);
-int64_t or_tasks(int32_t n, const int64_t* off, const int32_t* cols, int64_t small_max, int32_t* owner,
-                 int32_t* partner, int64_t* pos, int64_t* n_small);
-int or_task_costs(int model, int fn, int32_t piece, int64_t small_max, int32_t c_task, int32_t c_owner, int32_t n,
-                  const int32_t* deg, const int64_t* off, const int32_t* cols, int64_t T, const int32_t* owner,
-                  const int32_t* partner, uint64_t* cost);
 int64_t or_schedule(int64_t T, const uint64_t* cost, int64_t W, uint64_t min_chunk, uint64_t* cb, int64_t* tb,
                     int64_t cap);
 
@@ -75,24 +70,18 @@ static void run(const char* name, int32_t n, int64_t m, const int32_t* src, cons
         CHECK(s == T);
         free(tab);
     }
-    /* task decomposition, costs and the Eq. 1 / Eq. 2 chunk table */
-    int32_t* ow = malloc((size_t)(mh > 0 ? mh : 1) * 4);
-    int32_t* pa = malloc((size_t)(mh > 0 ? mh : 1) * 4);
-    int64_t* pos = malloc((size_t)(mh > 0 ? mh : 1) * 8);
-    int64_t ns = 0;
-    const int64_t Tk = or_tasks(n, off, cols, 64, ow, pa, pos, &ns);
-    CHECK(Tk >= 0 && ns <= Tk);
-    uint64_t* cost = malloc((size_t)(Tk > 0 ? Tk : 1) * 8);
-    for (int model = 0; model < 3; ++model)
-        CHECK(or_task_costs(model, 3, 2048, 64, 4, 32, n, deg, off, cols, Tk, ow, pa, cost) == 0);
+    /* the Eq. 1 / Eq. 2 chunk table over the merge cost d^_v + d^_u of every oriented edge */
+    uint64_t* cost = malloc((size_t)(mh > 0 ? mh : 1) * 8);
+    for (int32_t v = 0; v < n; ++v)
+        for (int64_t i = off[v]; i < off[v + 1]; ++i)
+            cost[i] = (uint64_t)(off[v + 1] - off[v]) + (uint64_t)(off[cols[i] + 1] - off[cols[i]]);
     const int64_t cap = 1 << 16;
     uint64_t* cb = malloc((size_t)cap * 8);
     int64_t* tb = malloc((size_t)cap * 8);
-    CHECK(or_schedule(Tk, cost, 7, 32, cb, tb, cap) >= 0);
-    printf("%s: n=%d m=%lld m_hat=%lld T=%llu tasks=%lld\n", name, n, (long long)m, (long long)mh,
-           (unsigned long long)T, (long long)Tk);
+    CHECK(or_schedule(mh, cost, 7, 32, cb, tb, cap) >= 0);
+    printf("%s: n=%d m=%lld m_hat=%lld T=%llu\n", name, n, (long long)m, (long long)mh, (unsigned long long)T);
     free(ea); free(eb); free(deg); free(off); free(cols); free(pe); free(tv); free(f);
-    free(ow); free(pa); free(pos); free(cost); free(cb); free(tb);
+    free(cost); free(cb); free(tb);
 }
 
 int main(void) {

@@ -1,8 +1,10 @@
 """GPU path vs the CPU oracle, element by element, through the C ABI.
 
 Integer results must match bit-exactly (tolerance 0): N+ lists and degrees (steps
-a1-a5), the task array and the schedule (a6), per-edge counts (a7), totals and
-T_v (a8).
+a1-a5), per-edge counts (a7), totals and T_v (a8) against the oracle; the chunk
+table (a6) against the oracle's Eq. 1 / Eq. 2 schedule.  The task array and the
+task costs are this library's own decomposition: they are checked against its
+restatement in tests/schedule_model.py, not against the oracle.
 """
 import numpy as np
 import pytest
@@ -10,6 +12,7 @@ import pytest
 import oracle
 from graphgen import families as F
 from graphgen import workloads as W
+from tests import schedule_model as M
 
 pytestmark = pytest.mark.gpu
 
@@ -91,11 +94,11 @@ SMALL_MAX = 64  # the default build option
 
 
 @pytest.mark.parametrize("name", list(GRAPHS))
-def test_tasks_match_oracle(built, name):
+def test_tasks_match_the_decomposition(built, name):
     g, csr = built[name]
     _, _, _, tasks = g.csr()
     t = tasks.cpu().numpy().astype(np.int64)
-    o, p, ns = oracle.tasks(csr, small_max=SMALL_MAX, with_split=True)
+    o, p, ns = M.tasks(csr, small_max=SMALL_MAX, with_split=True)
     assert g.info()["tasks_small"] == ns
     assert np.array_equal(t[:, 0], o) and np.array_equal(t[:, 1], p)
     assert np.array_equal(t[:, 2], csr.off[p]) and np.array_equal(t[:, 3], np.diff(csr.off)[p])
@@ -109,7 +112,7 @@ def test_small_max_build_option(small_max):
         with tc.Graph.build(s, d, n, tc.default_options(small_max=small_max)) as g:
             _, _, _, tasks = g.csr()
             t = tasks.cpu().numpy().astype(np.int64)
-            o, p, ns = oracle.tasks(csr, small_max=small_max, with_split=True)
+            o, p, ns = M.tasks(csr, small_max=small_max, with_split=True)
             assert g.info()["tasks_small"] == ns
             assert np.array_equal(t[:, 0], o) and np.array_equal(t[:, 1], p)
             assert g.count() == oracle.count(csr)
@@ -154,21 +157,22 @@ def _sorted_rows(x):
                                          (tc.TC_COST_DEGREE, 1024), (tc.TC_COST_PATRIC, 2048),
                                          (tc.TC_COST_NEW, 4096), (tc.TC_COST_ONE, 2048)])
 def test_schedule_matches_oracle(built, name, model, piece):
-    """Per class, the chunks the workers took are exactly Eq. 1 + Eq. 2 over the oracle's task costs."""
+    """Per class, the chunks the workers took are exactly the oracle's Eq. 1 + Eq. 2 schedule over
+    the task costs (the paper's merge and per-vertex costs, or this design's EDGE cost)."""
     g, csr = built[name]
     big_warps = 16 if piece <= 2048 else 8
     opt = tc.default_options(cost_model=model, piece=piece, warps_per_block=16, big_warps=big_warps)
     T, meta, chunks, busy = g.count_ex(opt, trace_cap=1 << 20, busy=True)
     assert T == oracle.count(csr)
-    o, p, ns = oracle.tasks(csr, small_max=SMALL_MAX, with_split=True)
+    o, p, ns = M.tasks(csr, small_max=SMALL_MAX, with_split=True)
     assert meta["tasks_small"] == ns
     if model == tc.TC_COST_EDGE:
-        cost = oracle.task_costs(csr, o, p, oracle.MODEL_EDGE, piece=piece, c_task=4, c_owner=32,
+        cost = M.task_costs(csr, o, p, M.MODEL_EDGE, piece=piece, c_task=4, c_owner=32,
                                  small_max=SMALL_MAX)
     elif model == tc.TC_COST_MERGE:
-        cost = oracle.task_costs(csr, o, p, oracle.MODEL_MERGE)
+        cost = M.task_costs(csr, o, p, M.MODEL_MERGE)
     else:
-        cost = oracle.task_costs(csr, o, p, oracle.MODEL_VERTEX, fn=model - tc.TC_COST_ONE)
+        cost = M.task_costs(csr, o, p, M.MODEL_VERTEX, fn=model - tc.TC_COST_ONE)
     got = chunks.cpu().numpy()
     n_want = 0
     for cls, (lo, hi) in enumerate(((0, ns), (ns, len(o)))):
@@ -367,7 +371,7 @@ def _streamed_entries(csr, small_max, piece, trim_min=None):
     partner list has at least trim_min entries, else the whole list."""
     from paper_1406_5687_gb300 import _lib
     trim_min = _lib.TC_TRIM_MIN_ENTRIES if trim_min is None else trim_min
-    own, par, ns = oracle.tasks(csr, small_max=small_max, with_split=True)
+    own, par, ns = M.tasks(csr, small_max=small_max, with_split=True)
     off, cols = csr.off, csr.cols.astype(np.int64)
     dh = np.diff(off)
     small = int(dh[par[:ns]].sum())
@@ -428,6 +432,41 @@ def test_partitioned_count_adds_up(name, nparts):
         parts = [g.count_partition(p, nparts) for p in range(nparts)]
         assert sum(parts) == want, parts
         assert g.count() == want  # the full count is unaffected
+
+
+def _part_counts(csr, nparts, model, piece=2048, small_max=SMALL_MAX):
+    """Per part, the oracle's per-edge counts (Theorem 1 attribution) summed over the oriented
+    edges of the tasks that part holds: per class, the tasks whose exclusive cost prefix lies in
+    [C p / P, C (p + 1) / P)."""
+    _, pe, _ = oracle.count(csr, per_edge=True, per_vertex=True)
+    o, p, ns, pos = M.tasks(csr, small_max=small_max, with_split=True, with_pos=True)
+    if model == tc.TC_COST_EDGE:
+        cost = M.task_costs(csr, o, p, M.MODEL_EDGE, piece=piece, c_task=4, c_owner=32, small_max=small_max)
+    elif model == tc.TC_COST_MERGE:
+        cost = M.task_costs(csr, o, p, M.MODEL_MERGE)
+    else:
+        cost = M.task_costs(csr, o, p, M.MODEL_VERTEX, fn=model - tc.TC_COST_ONE)
+    want = np.zeros(nparts, np.int64)
+    for lo, hi in ((0, ns), (ns, len(o))):
+        part = M.partition_members(cost[lo:hi], nparts)
+        np.add.at(want, part, pe[pos[lo:hi]].astype(np.int64))
+    return want
+
+
+@pytest.mark.parametrize("name", ["cl_200k", "cl_dense", "ba_30k", "book_5000"])
+@pytest.mark.parametrize("nparts", [2, 3, 7, 64])
+@pytest.mark.parametrize("model", [tc.TC_COST_EDGE, tc.TC_COST_MERGE, tc.TC_COST_DEGREE, tc.TC_COST_NEW])
+def test_each_partition_part_counts_its_own_tasks(name, nparts, model):
+    """Every part, not only their sum: part p's count equals the oracle's per-edge counts of
+    exactly the oriented edges whose tasks fall in part p, so no part counts a task twice
+    while another misses it."""
+    n, s, d = GRAPHS[name]
+    csr = oracle_csr(n, s, d)
+    want = _part_counts(csr, nparts, model)
+    with tc.Graph.build(s, d, n, tc.default_options(cost_model=model)) as g:
+        got = [g.count_partition(p, nparts) for p in range(nparts)]
+    assert got == want.tolist()
+    assert int(want.sum()) == oracle.count(csr)
 
 
 @pytest.mark.parametrize("options", [dict(cost_model=tc.TC_COST_DEGREE), dict(cost_model=tc.TC_COST_NEW),

@@ -1,12 +1,12 @@
-"""tc_count_static: counting with no device allocation, against tc_count.
+"""tc_count_static: counting with no device allocation, against the oracle and tc_count.
 
 Some callers cannot allocate device memory when they count -- their memory is owned
 by their own pool, or an allocation there could block or is not allowed.  For them
 the library offers tc_count_static, which keeps the count's scratch in a fixed device
 array declared by the library.  This file checks, through the C ABI, that two calls in
-a row give the same exact totals as tc_count (tolerance 0: counts are integers), that
-graphs with too many tasks are refused, and that the call takes no memory through the
-graph's allocator.  It is named so that pytest collects it last.
+a row give the oracle's exact total and the same total as tc_count (tolerance 0: counts
+are integers), that graphs with too many tasks are refused, and that the call takes no
+memory through the graph's allocator.  It is named so that pytest collects it last.
 """
 import ctypes
 
@@ -20,6 +20,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 import graphgen  # noqa: E402
+import oracle  # noqa: E402
 import paper_1406_5687_gb300 as tc  # noqa: E402
 from graphgen import families as F  # noqa: E402
 from paper_1406_5687_gb300 import _lib  # noqa: E402
@@ -35,6 +36,12 @@ def _graphs():
     s, d = graphgen.chung_lu(n, 2.05, 100.0, 1500.0, 150_000, 32)
     yield "chung_lu_dense", n, s, d
     yield "no_edges", 10, np.zeros(0, np.int32), np.zeros(0, np.int32)
+    # K_200: its lists hold 199, 198, ..., 0 entries, so owners fall in both task classes
+    n, s, d = F.complete(200)
+    yield "complete_200", n, s, d
+
+
+CASES = 5
 
 
 def _static_count(lib, g, out, stream):
@@ -44,13 +51,19 @@ def _static_count(lib, g, out, stream):
     return int(out.item())
 
 
-@pytest.mark.parametrize("case", list(range(4)))
-def test_two_calls_match_tc_count(case):
+@pytest.mark.parametrize("case", list(range(CASES)))
+def test_two_calls_match_the_oracle_and_tc_count(case):
     name, n, s, d = list(_graphs())[case]
+    want = oracle.count_edges(n, s, d)
+    if name == "complete_200":
+        assert want == 200 * 199 * 198 // 6  # C(n, 3)
     lib = _lib.load()
     with tc.Graph.build(s, d, n) as g:
-        assert g.info()["tasks"] <= _lib.TC_COUNT_STATIC_MAX_TASKS, name
-        want = g.count()
+        info = g.info()
+        assert info["tasks"] <= _lib.TC_COUNT_STATIC_MAX_TASKS, name
+        if name == "complete_200":
+            assert 0 < info["tasks_small"] < info["tasks"]  # small and big owners both present
+        assert g.count() == want
         out = torch.full((1,), -1, dtype=torch.int64, device="cuda")
         stream = torch.cuda.Stream()
         first = _static_count(lib, g, out, stream)
