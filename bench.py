@@ -271,6 +271,38 @@ def algorithmic_bytes(g, opt):
             "untrimmed_big_entries": int(info["sum_stream"]) - int(streamed[0])}
 
 
+def _bits_for(x):
+    """Bits of the largest id below x (at least 1), as the library sizes its keys."""
+    return max(1, int(x - 1).bit_length()) if x > 1 else 1
+
+
+def build_bytes(info):
+    """Compulsory DRAM bytes of one build (steps a1-a5 and the task array), counting each
+    streamed array access once and the random-access arrays (degrees, offsets, numbering) once
+    by their size: k_canon reads 8 and writes 8 per input pair; every onesweep pass reads and
+    writes 8 per key (the 48-bit edge keys: 2b bits, the oriented keys: the b owner bits, the
+    task keys: bits(n + 1)); the dedupe pass and the orienting compaction read the sorted keys
+    (8 each) and write 8 per distinct edge; the lists' last pass also writes cols (4); the task
+    keys read 8 and write 8 per oriented edge; the task sort's last pass writes 16-byte records
+    instead of keys; the owner index reads the records' owners (4 per task, twice)."""
+    m, mh, T, n = int(info["m_input"]), int(info["m_hat"]), int(info["tasks"]), int(info["n"])
+    b = _bits_for(n)
+    p1, p2, p3 = -(-2 * b // 8), -(-b // 8), -(-_bits_for(n + 1) // 8)
+    terms = {
+        "canon": 16 * m,
+        "sort_edges": 16 * p1 * m,
+        "dedupe_degree": 8 * m + 8 * n,
+        "orient_compact": 8 * m + 8 * mh + 4 * n,
+        "sort_lists": 16 * p2 * mh + 4 * mh,
+        "offsets": 4 * n + 8 * (n + 1),
+        "task_keys": 16 * mh + 12 * n,
+        "sort_tasks": 16 * (p3 - 1) * mh + 8 * mh + 16 * T + 8 * (n + 1) + 4 * n,
+        "owner_index": 8 * T,
+    }
+    return {"bytes": sum(terms.values()), "terms": terms, "sort_passes": [p1, p2, p3],
+            "sort_bytes": 16 * (p1 * m + (p2 + p3) * mh)}
+
+
 def cpu_baseline(workload, sample_pairs, single_thread_budget_s=60.0):
     """The oracle as it stands (simple graph, Fig. 1 lists, Fig. 1 count) on the whole benched
     graph, timed on the host: the simple graph and the lists as the oracle builds them (one
@@ -1111,6 +1143,12 @@ def run_gpu(args, rank, world, local):
                                 "note": "4 (sum over oriented edges of |N+(u)| + m_hat) + 16 n per count, "
                                         "over both count kernels"}}
 
+    bb = build_bytes(dict(info, m_input=m_in))
+    build_roofline = {"phase": "build (a1-a5 and the task array)", "bound": "hbm", "bytes": bb["bytes"],
+                      "ms": build_ms, "achieved": bb["bytes"] / (build_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                      "frac": bb["bytes"] / (build_ms / 1e3) / 1e9 / peak, "peak_source": f"hbm_gbs of {peak_kind}",
+                      "sort_passes": bb["sort_passes"], "sort_bytes": bb["sort_bytes"], "terms": bb["terms"]}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, CPU_SAMPLE_PAIRS[args.workload])
@@ -1139,7 +1177,8 @@ def run_gpu(args, rank, world, local):
                               "count_kernels": kernel_ms, "count_kernel_small": small_ms, "count_kernel_big": big_ms},
                 "count_only": {"value": m_hat / (count_ms / 1e3), "unit": UNIT,
                                "note": "m_hat / (cost prefix + schedule + intersection), lists resident"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roofline, "build_roofline": build_roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches,
                 "clocks": clk, "work": {"small": alg["small"], "big": alg["big"]}, "wall_s_timed": t_wall,
                 "per_vertex": extras, "surrogate": surrogate, "batch": batch, "serve": serve}
         print(json.dumps(line), flush=True)

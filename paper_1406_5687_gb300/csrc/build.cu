@@ -129,52 +129,122 @@ __global__ void k_canon(const int32_t* __restrict__ src, const int32_t* __restri
     digit_counts_flush(dc, dc_sh);
 }
 
-struct UniquePred {
-    const uint64_t* k;
-    uint64_t sent;
-    __device__ bool operator()(int64_t i) const { return k[i] != sent && (i == 0 || k[i] != k[i - 1]); }
-};
-struct KeyVal {
-    const uint64_t* k;
-    __device__ uint64_t operator()(int64_t i) const { return k[i]; }
-};
+// --------------------------------------------------------------------------- a2-a4
+// Degrees (a3) come in two halves.  The pass of the edge sort that completes the larger
+// endpoint's bits leaves the keys ordered by it, and its writer adds one count per run of
+// equal larger endpoints (duplicates included).  After the sort one pass over the keys counts
+// each tile's distinct keys (a key is kept when it is not the sentinel and differs from the
+// key before it), adds the kept keys' runs of equal smaller endpoints, and takes each repeated
+// key back from its larger endpoint.  After a scan of the tile counts, a second pass orients
+// every kept edge by the finished degrees (a4) and writes it at its compacted position,
+// counting the digits of the oriented keys for the next sort.
 
-// --------------------------------------------------------------------------- a3: degrees
-__global__ void k_degree(const uint64_t* __restrict__ ukeys, int64_t mh, int b, int32_t* __restrict__ deg) {
-    const uint64_t mask = (1ull << b) - 1;
-    const int lane = threadIdx.x & 31;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i - lane < mh;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        bool in = i < mh;
-        uint64_t k = in ? ukeys[i] : 0;
-        uint32_t a = in ? (uint32_t)(k >> b) : 0xFFFFFFFFu;
-        // keys are sorted by their smaller endpoint, so equal ones form runs of lanes: the
-        // first lane of each run adds the run's length
-        const uint32_t prev = __shfl_up_sync(kFull, a, 1);
-        const bool head = in && (lane == 0 || a != prev);
-        const unsigned heads = __ballot_sync(kFull, head);
-        const int n_in = __popc(__ballot_sync(kFull, in));  // valid lanes are 0 .. n_in - 1
-        const unsigned after = heads & ~lanemask_le();
-        const int run_end = after ? __ffs(after) - 1 : n_in;
-        if (head) atomicAdd(&deg[a], run_end - lane);
-        if (in) atomicAdd(&deg[(uint32_t)(k & mask)], 1);
+// The larger-endpoint half one key at a time (only when the sort ran no pass: m <= 1).
+__global__ void k_degree_larger(const uint64_t* __restrict__ keys, int64_t n, uint64_t sent, int b,
+                                int32_t* __restrict__ deg) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (keys[i] != sent) atomicAdd(&deg[(uint32_t)(keys[i] & ((1ull << b) - 1))], 1);
+}
+
+// Keys of a warp's rows and, for each, the key before it.
+__device__ __forceinline__ void load_rows(const uint64_t* __restrict__ keys, int64_t base, int64_t n, uint64_t sent,
+                                          int lane, uint64_t (&x)[kCpItems], uint64_t (&xp)[kCpItems]) {
+#pragma unroll
+    for (int k = 0; k < kCpItems; ++k) {
+        const int64_t i = base + k * 32 + lane;
+        x[k] = i < n ? __ldg(&keys[i]) : sent;
+        xp[k] = (i > 0 && i < n) ? __ldg(&keys[i - 1]) : ~x[k];
     }
 }
 
-// --------------------------------------------------------------------------- a4: orientation
-__global__ void k_orient(const uint64_t* __restrict__ ukeys, int64_t mh, int b, const int32_t* __restrict__ deg,
-                         uint64_t* __restrict__ okeys, DigitCounts dc) {
+__global__ void __launch_bounds__(kCpBlock) k_dedupe_degree(const uint64_t* __restrict__ keys, int64_t n, uint64_t sent,
+                                                            int b, int32_t* __restrict__ deg, uint32_t* tile_counts) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kCpTile + (int64_t)warp * 32 * kCpItems;
+    const uint64_t mask = (1ull << b) - 1;
+    uint64_t x[kCpItems], xp[kCpItems];
+    load_rows(keys, base, n, sent, lane, x, xp);
+    uint32_t c = 0;
+    // the smaller endpoints of kept keys form runs (keys are sorted).  A hub's run covers many
+    // rows, so the run still open at a row's end is carried into the next row (cv, cc, the same
+    // in every lane) and added once when it closes: one atomic per run per warp, not per row.
+    uint32_t cv = 0xFFFFFFFFu;
+    int cc = 0;
+#pragma unroll
+    for (int k = 0; k < kCpItems; ++k) {
+        const bool real = x[k] != sent;  // past the end, x is the sentinel
+        const bool keep = real && x[k] != xp[k];
+        const unsigned kb = __ballot_sync(kFull, keep);
+        c += __popc(kb);
+        const uint32_t a = keep ? (uint32_t)(x[k] >> b) : 0xFFFFFFFFu;
+        const uint32_t pa = __shfl_up_sync(kFull, a, 1);
+        const bool edge = lane == 0 || a != pa;
+        const unsigned after = __ballot_sync(kFull, edge) & ~lanemask_le();
+        const int end = after ? __ffs(after) - 1 : 32;
+        const uint32_t a0 = __shfl_sync(kFull, a, 0), a31 = __shfl_sync(kFull, a, 31);
+        const bool continues = (kb & 1u) && a0 == cv;  // lane 0's run extends the carried one
+        if (!continues && cc > 0 && lane == 0) atomicAdd(&deg[cv], cc);
+        const bool open = (kb >> 31) & 1u;             // the row ends inside a run of kept keys
+        const unsigned heads = __ballot_sync(kFull, keep && edge);
+        const int h = open ? 31 - __clz(heads) : 32;   // head of the run reaching lane 31
+        if (keep && edge && lane != h) atomicAdd(&deg[a], end - lane + ((lane == 0 && continues) ? cc : 0));
+        cc = open ? 32 - h + ((h == 0 && continues) ? cc : 0) : 0;
+        cv = open ? a31 : 0xFFFFFFFFu;
+        if (real && !keep) atomicSub(&deg[(uint32_t)(x[k] & mask)], 1);  // a repeat, counted by the sort
+    }
+    if (cc > 0 && lane == 0) atomicAdd(&deg[cv], cc);
+    __shared__ uint32_t ws[kCpBlock / 32];
+    if (lane == 0) ws[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kCpBlock / 32; ++w) t += ws[w];
+        tile_counts[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kCpBlock) k_orient_compact(const uint64_t* __restrict__ keys, int64_t n, uint64_t sent,
+                                                             int b, const int32_t* __restrict__ deg,
+                                                             const uint64_t* __restrict__ tile_prefix,
+                                                             uint64_t* __restrict__ okeys, DigitCounts dc) {
     extern __shared__ unsigned dc_sh[];
     digit_counts_init(dc, dc_sh);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kCpTile + (int64_t)warp * 32 * kCpItems;
     const uint64_t mask = (1ull << b) - 1;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mh; i += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t k = ukeys[i];
-        uint32_t a = (uint32_t)(k >> b), c = (uint32_t)(k & mask);  // a < c
-        int32_t da = deg[a], dcd = deg[c];
-        bool a_first = da < dcd || (da == dcd);  // equal degrees: the smaller id a comes first
-        const uint64_t o = a_first ? k : (((uint64_t)c << b) | a);
-        okeys[i] = o;
-        digit_counts_add(dc, dc_sh, o);
+    uint64_t x[kCpItems], xp[kCpItems];
+    load_rows(keys, base, n, sent, lane, x, xp);
+    unsigned bal[kCpItems];
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kCpItems; ++k) {
+        bal[k] = __ballot_sync(kFull, x[k] != sent && x[k] != xp[k]);
+        c += __popc(bal[k]);
+    }
+    __shared__ uint32_t ws[kCpBlock / 32];
+    if (lane == 0) ws[warp] = c;
+    // the degrees of both endpoints of every kept key, gathered before any write
+    int32_t da[kCpItems], dcn[kCpItems];
+#pragma unroll
+    for (int k = 0; k < kCpItems; ++k) {
+        const bool keep = (bal[k] >> lane) & 1u;
+        da[k] = keep ? __ldg(&deg[(uint32_t)(x[k] >> b)]) : 0;
+        dcn[k] = keep ? __ldg(&deg[(uint32_t)(x[k] & mask)]) : 0;
+    }
+    __syncthreads();
+    uint64_t pos = tile_prefix[blockIdx.x];
+    for (int w = 0; w < warp; ++w) pos += ws[w];
+#pragma unroll
+    for (int k = 0; k < kCpItems; ++k) {
+        if ((bal[k] >> lane) & 1u) {
+            const uint32_t a = (uint32_t)(x[k] >> b), cc = (uint32_t)(x[k] & mask);
+            // u < v iff d_u < d_v or (d_u = d_v and u < v): a < cc, so a comes first unless
+            // its degree is larger
+            const uint64_t o = da[k] <= dcn[k] ? x[k] : (((uint64_t)cc << b) | a);
+            okeys[pos + __popc(bal[k] & lanemask_lt())] = o;
+            digit_counts_add(dc, dc_sh, o);
+        }
+        pos += __popc(bal[k]);
     }
     digit_counts_flush(dc, dc_sh);
 }
@@ -248,7 +318,7 @@ __global__ void k_renumber(const int32_t* __restrict__ dhat, int small_max, cons
 
 // Task key: partner in the low 32 bits, the owner's number above.  The stable sort on the
 // number alone keeps each owner's tasks in the order of their oriented edges in the lists.
-__global__ void k_task_keys(const uint64_t* __restrict__ okeys, const int32_t* __restrict__ cols, int64_t mh, int b,
+__global__ void k_task_keys(const uint64_t* __restrict__ okeys, int64_t mh, int b,
                             const int32_t* __restrict__ dhat, int small_max, const uint32_t* __restrict__ rid,
                             int32_t n, uint64_t* __restrict__ tkeys, BuildCounters* cnt, DigitCounts dcn) {
     extern __shared__ unsigned dc_sh[];
@@ -256,8 +326,9 @@ __global__ void k_task_keys(const uint64_t* __restrict__ okeys, const int32_t* _
     const int lane = threadIdx.x & 31;
     unsigned long long sv = 0, su = 0, ss = 0, nt = 0, nsm = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mh; i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t v = (uint32_t)(okeys[i] >> b);
-        uint32_t u = (uint32_t)cols[i];
+        const uint64_t ok = okeys[i];
+        const uint32_t v = (uint32_t)(ok >> b);
+        const uint32_t u = (uint32_t)(ok & ((1ull << b) - 1ull));
         int32_t dv = dhat[v], du = dhat[u];
         uint32_t o = dv >= du ? v : u, p = dv >= du ? u : v;
         int32_t dp = dv >= du ? du : dv;
@@ -394,13 +465,44 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         note_launch();
     }
     TC_CUDA_TRY(cudaGetLastError());
-    // a2
+    // a2, with the larger-endpoint half of a3 counted by the pass that completes those bits
+    DevBuf<int32_t> deg, dhat;
+    TC_TRY(deg.alloc(al, n > 0 ? n : 1, s));
+    TC_TRY(dhat.alloc(al, n > 0 ? n : 1, s));
+    TC_CUDA_TRY(cudaMemsetAsync(deg.ptr, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));
+    TC_CUDA_TRY(cudaMemsetAsync(dhat.ptr, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));
+    OsOut larger;
+    larger.mode = OS_OUT_RUNS;
+    larger.pass = sort_passes(b) - 1;
+    larger.fshift = 0;
+    larger.fmask = (1ull << b) - 1;
+    larger.skip = sent;
+    larger.cnt = deg.ptr;
+    larger.nvert = (uint32_t)n;
     uint64_t* sorted = nullptr;
-    TC_TRY(radix_sort_u64(ka.ptr, kb.ptr, m, 0, nbits, al, s, &sorted, g->status, spin, m > 0 ? ucounts : nullptr));
-    TC_TRY(check_device_error(g, s));
+    bool larger_done = false;
+    TC_TRY(radix_sort_u64(ka.ptr, kb.ptr, m, 0, nbits, al, s, &sorted, g->status, spin, m > 0 ? ucounts : nullptr,
+                          &larger, &larger_done));
+    TC_TRY(check_device_error(g, s));  // the sorted keys are read only if every wait of the sort ended
     uint64_t* other = sorted == ka.ptr ? kb.ptr : ka.ptr;
+    if (m > 0 && !larger_done) {
+        k_degree_larger<<<grid_stride_blocks(m), kThreads, 0, s>>>(sorted, m, sent, b, deg.ptr);
+        note_launch();
+    }
+    const int64_t ctiles = ceil_div(m > 0 ? m : 1, kCpTile);
+    DevBuf<uint32_t> tcount;
+    DevBuf<uint64_t> tprefix, tscr;
+    TC_TRY(tcount.alloc(al, ctiles, s));
+    TC_TRY(tprefix.alloc(al, ctiles + 1, s));
+    TC_TRY(tscr.alloc(al, scan_scratch_words(ctiles), s));
     uint64_t mh64 = 0;
-    TC_TRY(compact(UniquePred{sorted, sent}, KeyVal{sorted}, m, other, al, s, &mh64));
+    if (m > 0) {
+        k_dedupe_degree<<<(unsigned)ctiles, kCpBlock, 0, s>>>(sorted, m, sent, b, deg.ptr, tcount.ptr);
+        note_launch();
+        TC_CUDA_TRY(cudaGetLastError());
+        TC_CUDA_TRY(scan_exclusive(IdentityU32Scan{tcount.ptr}, ctiles, tprefix.ptr, tscr.ptr, s));
+        TC_CUDA_TRY(cudaMemcpyAsync(&mh64, tprefix.ptr + ctiles, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    }
     BuildCounters hc;
     TC_CUDA_TRY(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(hc), cudaMemcpyDeviceToHost, s));
     TC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -415,41 +517,43 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     g->duplicates = m - g->self_loops - mh;
     if (g->opt.input_policy == TC_INPUT_STRICT && (g->self_loops > 0 || g->duplicates > 0)) return TC_ERR_INVALID_ARG;
     if (mh >= (int64_t)0xFFFFFFFFll) return TC_ERR_UNSUPPORTED;  // task records index lists with uint32
-    uint64_t* ukeys = other;   // mh distinct keys
+    // a4: orient the distinct edges into the other key buffer, compacted
+    uint64_t* okeys = other;
     uint64_t* spare = sorted;  // free buffer of m keys
-
-    // a3
-    DevBuf<int32_t> deg, dhat;
-    TC_TRY(deg.alloc(al, n > 0 ? n : 1, s));
-    TC_TRY(dhat.alloc(al, n > 0 ? n : 1, s));
-    TC_CUDA_TRY(cudaMemsetAsync(deg.ptr, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));
-    TC_CUDA_TRY(cudaMemsetAsync(dhat.ptr, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));
-    if (mh > 0) {
-        k_degree<<<grid_stride_blocks(mh), kThreads, 0, s>>>(ukeys, mh, b, deg.ptr);
-        note_launch();
-    }
-    // a4
     if (mh > 0) {
         const DigitCounts dc{ucounts, b, sort_passes(b)};
         TC_TRY(zero_counts(dc, s));
-        k_orient<<<count_blocks(mh), kThreads, digit_counts_bytes(dc), s>>>(ukeys, mh, b, deg.ptr, spare, dc);
+        k_orient_compact<<<(unsigned)ctiles, kCpBlock, digit_counts_bytes(dc), s>>>(sorted, m, sent, b, deg.ptr,
+                                                                                   tprefix.ptr, okeys, dc);
         note_launch();
     }
     TC_CUDA_TRY(cudaGetLastError());
+    tcount.release();
+    tprefix.release();
+    tscr.release();
     // a5: group the oriented edges by owner.  The distinct keys arrive sorted by (min, max),
     // so a stable sort on the owner bits alone leaves every list ascending: an owner v's
     // partners below v come from earlier runs (keys (u, v), u ascending), its partners above v
-    // from v's own run (keys (v, x), x ascending), in that order.
-    uint64_t* osorted = nullptr;
-    TC_TRY(radix_sort_u64(spare, ukeys, mh, b, b, al, s, &osorted, g->status, spin, mh > 0 ? ucounts : nullptr));
-    TC_TRY(check_device_error(g, s));
-    uint64_t* free_buf = osorted == spare ? ukeys : spare;
-    // a5
+    // from v's own run (keys (v, x), x ascending), in that order.  The last pass also writes
+    // the lists (cols) and counts each owner's entries (d^).
     DevBuf<int64_t> off;
     DevBuf<int32_t> cols;
     TC_TRY(off.alloc(al, (size_t)n + 1, s));
     TC_TRY(cols.alloc(al, (size_t)(mh > 0 ? mh : 1) + 4, s));  // +4: 16-byte vector reads may run past the end
-    if (mh > 0) {
+    OsOut lists_out;
+    lists_out.mode = OS_OUT_LISTS;
+    lists_out.b = b;
+    lists_out.cols = cols.ptr;
+    lists_out.fshift = b;
+    lists_out.cnt = dhat.ptr;
+    lists_out.nvert = (uint32_t)n;
+    uint64_t* osorted = nullptr;
+    bool lists_done = false;
+    TC_TRY(radix_sort_u64(okeys, spare, mh, b, b, al, s, &osorted, g->status, spin, mh > 0 ? ucounts : nullptr,
+                          &lists_out, &lists_done));
+    TC_TRY(check_device_error(g, s));
+    uint64_t* free_buf = osorted == okeys ? spare : okeys;
+    if (mh > 0 && !lists_done) {
         k_lists<<<grid_stride_blocks(mh), kThreads, 0, s>>>(osorted, mh, b, dhat.ptr, cols.ptr);
         note_launch();
     }
@@ -482,19 +586,19 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         const DigitCounts dc{ucounts, 32, sort_passes(task_bits)};
         TC_TRY(zero_counts(dc, s));
         k_task_keys<<<count_blocks(mh), kThreads, digit_counts_bytes(dc), s>>>(
-            osorted, cols.ptr, mh, b, dhat.ptr, g->opt.small_max, rid.ptr, n, free_buf, cnt.ptr, dc);
+            osorted, mh, b, dhat.ptr, g->opt.small_max, rid.ptr, n, free_buf, cnt.ptr, dc);
         note_launch();
     }
     TC_CUDA_TRY(cudaGetLastError());
-    uint64_t* tsorted = nullptr;
-    TC_TRY(radix_sort_u64(free_buf, osorted, mh, 32, task_bits, al, s, &tsorted, g->status, spin,
-                          mh > 0 ? ucounts : nullptr));
-    TC_TRY(check_device_error(g, s));
     TC_CUDA_TRY(cudaMemcpyAsync(&hc, cnt.ptr, sizeof(hc), cudaMemcpyDeviceToHost, s));
     TC_CUDA_TRY(cudaStreamSynchronize(s));
     const int64_t T = (int64_t)hc.tasks;
     DevBuf<TaskRec> rec;
     TC_TRY(rec.alloc(al, T > 0 ? T : 1, s));
+    uint64_t* tsorted = nullptr;
+    TC_TRY(radix_sort_u64(free_buf, osorted, mh, 32, task_bits, al, s, &tsorted, g->status, spin,
+                          mh > 0 ? ucounts : nullptr));
+    TC_TRY(check_device_error(g, s));
     if (T > 0) {
         k_task_records<<<grid_stride_blocks(T), kThreads, 0, s>>>(tsorted, T, inv.ptr, off.ptr, rec.ptr);
         note_launch();

@@ -742,7 +742,18 @@ __device__ __forceinline__ void block_worker(const CountArgs& a, Process process
         const unsigned long long q = H / W, r = H % W, w0 = (unsigned long long)wid;
         const unsigned long long lo = w0 * q + (w0 < r ? w0 : r);
         const unsigned long long hi = (w0 + 1) * q + (w0 + 1 < r ? w0 + 1 : r);
-        const long long t0 = wid == 0 && a.sched->at_start ? a.t_begin : class_bound(a, lo, C, base, lane);
+        // worker 0 starts at the schedule's first task: the class's first, or for a later part the
+        // first task whose prefix reaches the part's base -- even when the part's cost is zero, where
+        // its start boundary would otherwise map to the class end and its zero-cost tasks be lost
+        long long t0;
+        if (wid == 0 && a.sched->at_start) {
+            t0 = a.t_begin;
+        } else if (wid == 0) {
+            const uint64_t* __restrict__ P = a.P;
+            t0 = warp_first_true(a.t_begin, a.t_end, [&](long long q) { return P[q] >= base; }, lane);
+        } else {
+            t0 = class_bound(a, lo, C, base, lane);
+        }
         const long long t1 = class_bound(a, hi, C, base, lane);
         if (lane == 0) {
             s_t[0] = t0;
