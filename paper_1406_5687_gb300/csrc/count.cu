@@ -424,10 +424,12 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
             if (!EXTRA) {
                 uint32_t more;
                 cnt += probe_batch<4>(hv, xs, ok, more);
-                while (more) {
-                    const int k = __ffs(more) - 1;
-                    more &= more - 1;
-                    cnt += hash_probe_rest(hv, xs[k], (hash_start(hv, xs[k]) + 2) & hv.cmask) ? 1u : 0u;
+                // entries whose first bucket held two other keys (rare); every index is static so
+                // that the four entries stay in registers
+                if (more) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if ((more >> k) & 1u) cnt += hash_probe_rest(hv, xs[k], (hash_start(hv, xs[k]) + 2) & hv.cmask) ? 1u : 0u;
                 }
             } else {
                 uint32_t h = 0;
