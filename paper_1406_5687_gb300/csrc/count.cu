@@ -40,7 +40,6 @@ constexpr uint32_t kHashMul = 0x9E3779B1u;  // Knuth's multiplicative constant, 
 #define TC_UNITS 4
 #endif
 constexpr int kUnits = TC_UNITS;  // 16-byte units of partner lists a lane loads per step of warp_batch_count
-constexpr int kTvCacheLog = 11;   // 2048 (vertex, count) slots per block for per-vertex counts
 
 struct CountArgs {
     const int64_t* off;
@@ -69,8 +68,8 @@ struct CountArgs {
     long long n_owners;         // big class: owners
     const int64_t* gtask;       // packs: this class's first task of each graph, then its end
     unsigned long long* streamed;  // traced counts only: partner entries read, summed per class
-    int cache_log;                 // per-vertex counts: log2 slots of the block's T_v cache (0: none)
-    int cache_off;                 // its offset in the block's dynamic shared memory, in words
+    int cnt_off;                   // per-vertex counts: words from a table slot to its hit count (0: none)
+    int hits_off;                  // per-vertex / per-edge counts: the warps' task-hit counters, in words
     long long n_sub;            // packs: graphs (0: one graph, one total)
 };
 
@@ -123,48 +122,12 @@ __device__ __forceinline__ long long edge_position(const CountArgs& a, uint32_t 
 // The block's dynamic shared memory: hash tables, then (per-vertex counts) the T_v cache.
 extern __shared__ uint32_t smem_dyn[];
 
-// Hub vertices close a great many triangles, and global atomics on one address serialise.
-// A block therefore keeps a small direct-mapped cache of (vertex, count) in shared memory:
-// a vertex takes a free slot on its first increment and later ones add there; a vertex
-// whose slot is taken goes to global memory.  The block adds the cache to T_v at its end.
-__device__ __forceinline__ void add_tv(const CountArgs& a, uint32_t w) {
-    if (a.cache_log) {
-        uint32_t* tags = smem_dyn + a.cache_off;
-        uint32_t* cnts = tags + (1u << a.cache_log);
-        const uint32_t sl = (w * kHashMul) >> (32 - a.cache_log);
-        uint32_t t = tags[sl];
-        if (t == kEmpty) t = atomicCAS(&tags[sl], kEmpty, w);
-        if (t == w || t == kEmpty) {
-            atomicAdd(&cnts[sl], 1u);
-            return;
-        }
-    }
-    atomicAdd(&a.t_v[w], 1ull);
-}
-
-__device__ __forceinline__ void tv_cache_init(const CountArgs& a) {
-    if (!a.cache_log) return;
-    uint32_t* tags = smem_dyn + a.cache_off;
-    for (uint32_t i = threadIdx.x; i < (1u << a.cache_log); i += blockDim.x) {
-        tags[i] = kEmpty;
-        tags[i + (1u << a.cache_log)] = 0u;
-    }
-    __syncthreads();
-}
-
-__device__ __forceinline__ void tv_cache_flush(const CountArgs& a) {
-    if (!a.cache_log) return;
-    __syncthreads();
-    const uint32_t* tags = smem_dyn + a.cache_off;
-    for (uint32_t i = threadIdx.x; i < (1u << a.cache_log); i += blockDim.x) {
-        const uint32_t c = tags[i + (1u << a.cache_log)];
-        if (tags[i] != kEmpty && c) atomicAdd(&a.t_v[tags[i]], (unsigned long long)c);
-    }
-}
-
-// Per-vertex and per-edge outputs.  Every hit w of a task (owner, partner) adds 1 to T_w;
-// the task's own vertices and its oriented edge gain the task's hits, which the warp sums
-// per task before one atomic each (flush_task_hits).
+// Per-vertex and per-edge outputs.  A triangle found at task (owner, partner) with third vertex
+// w adds 1 to T_owner, T_partner and T_w (Theorem 1's attribution) and 1 to its oriented edge.
+// Every w is an entry of the owner's staged list, so its hits are counted at w's own table slot
+// (a count array beside the table, one shared atomic per hit) and added to T_w once per staged
+// list.  A task's hits are summed in the warp's shared counter of that task and added to its
+// owner, its partner and its edge once per batch.
 __device__ __forceinline__ long long oriented_edge_position(const CountArgs& a, uint32_t owner, uint32_t partner) {
     // the oriented edge runs from whichever endpoint comes first in the degree order
     const int32_t dox = a.deg[owner], dpx = a.deg[partner];
@@ -172,26 +135,8 @@ __device__ __forceinline__ long long oriented_edge_position(const CountArgs& a, 
     return edge_position(a, owner_first ? owner : partner, owner_first ? partner : owner);
 }
 
-// Lanes holding units of the same task carry the same key and are adjacent: a segmented
-// suffix sum leaves each task's hits in its first lane, which adds them once.
-__device__ __forceinline__ void flush_task_hits(const CountArgs& a, uint32_t h, int key, uint32_t owner, uint32_t partner,
-                                                long long epos, int lane) {
-    uint32_t sum = h;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_down_sync(kFull, sum, o);
-        const int tk = __shfl_down_sync(kFull, key, o);
-        if (lane + o < 32 && tk == key) sum += t;
-    }
-    const int pk = __shfl_up_sync(kFull, key, 1);
-    const bool head = lane == 0 || pk != key;
-    if (head && key < 32 && sum != 0u) {
-        if (a.t_v) {
-            atomicAdd(&a.t_v[owner], (unsigned long long)sum);
-            atomicAdd(&a.t_v[partner], (unsigned long long)sum);
-        }
-        if (a.per_edge) atomicAdd(&a.per_edge[epos], sum);
-    }
+__device__ __forceinline__ uint32_t* warp_task_hits(const CountArgs& a) {
+    return smem_dyn + a.hits_off + 32 * (threadIdx.x >> 5);
 }
 
 struct HashView {
@@ -238,6 +183,41 @@ __device__ __forceinline__ bool hash_probe(const HashView& hv, uint32_t w) {
     return hash_probe_rest(hv, w, (h + 2) & hv.cmask);
 }
 
+// Slot of w in the table, or -1.
+__device__ __noinline__ int hash_find_rest(const HashView& hv, uint32_t w, uint32_t h) {
+    for (;;) {
+        const uint32_t s = hv.tbl[h];
+        if (s == w) return (int)h;
+        if (s == kEmpty) return -1;
+        h = (h + 1) & hv.cmask;
+    }
+}
+
+__device__ __forceinline__ int hash_find(const HashView& hv, uint32_t w) {
+    const uint32_t h = hash_start(hv, w);
+    const uint2 b = *reinterpret_cast<const uint2*>(hv.tbl + h);
+    if (b.x == w) return (int)h;
+    if (b.y == w) return (int)h + 1;
+    if (b.x == kEmpty || b.y == kEmpty) return -1;
+    return hash_find_rest(hv, w, (h + 2) & hv.cmask);
+}
+
+// Add the hit counts of a staged list's entries to T_v (one atomic per entry that was hit)
+// and clear them; entries [e0, ol) step `step` of the list at cols[ob].
+__device__ __forceinline__ void flush_slot_hits(const CountArgs& a, const HashView& hv, long long ob, uint32_t ol,
+                                                uint32_t e0, uint32_t step) {
+    for (uint32_t e = e0; e < ol; e += step) {
+        const uint32_t x = (uint32_t)__ldg(&a.cols[ob + e]);
+        const int sl = hash_find(hv, x);
+        if (sl < 0) continue;
+        uint32_t* c = hv.tbl + a.cnt_off + sl;
+        if (*c) {
+            atomicAdd(&a.t_v[x], (unsigned long long)*c);
+            *c = 0u;
+        }
+    }
+}
+
 // First-bucket lookups of N entries issued together.  Returns the hits; entries whose
 // bucket held two other keys are flagged in `more` (bit k) for hash_probe_rest.
 template <int N>
@@ -259,6 +239,26 @@ __device__ __forceinline__ uint32_t probe_batch(const HashView& hv, const uint32
         more |= (valid[k] && !hit && !end) ? (1u << k) : 0u;
     }
     return hits;
+}
+
+// First-bucket lookups of N entries issued together, returning each entry's slot (-1: absent);
+// entries whose bucket held two other keys are flagged in `more` for hash_find_rest.
+template <int N>
+__device__ __forceinline__ void find_batch(const HashView& hv, const uint32_t (&w)[N], const bool (&valid)[N],
+                                           int (&slot)[N], uint32_t& more) {
+    uint32_t h[N];
+    uint2 b[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) h[k] = hash_start(hv, w[k]);
+#pragma unroll
+    for (int k = 0; k < N; ++k) b[k] = *reinterpret_cast<const uint2*>(hv.tbl + h[k]);
+    more = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        slot[k] = !valid[k] ? -1 : b[k].x == w[k] ? (int)h[k] : b[k].y == w[k] ? (int)h[k] + 1 : -1;
+        const bool end = b[k].x == kEmpty || b[k].y == kEmpty;
+        more |= (valid[k] && slot[k] < 0 && !end) ? (1u << k) : 0u;
+    }
 }
 
 // Bit position of the set bit of m that has exactly k set bits below it (0 <= k < popc(m)):
@@ -376,8 +376,7 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
         const uint32_t tot = warp_sum(len);
         if (lane == 0 && tot) atomicAdd(a.streamed, (unsigned long long)tot);
     }
-    long long epos = 0;
-    if (EXTRA && a.per_edge && len != 0u) epos = oriented_edge_position(a, r.owner, r.partner);
+    uint32_t* thits = EXTRA ? warp_task_hits(a) : nullptr;
     const uint32_t units = len != 0u ? (((ps & 3u) + len + 3u) >> 2) : 0u;
     const uint32_t uincl = warp_inclusive_scan(units, lane);
     const uint32_t ustart = uincl - units;
@@ -386,8 +385,6 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
     for (uint32_t w0 = 0; w0 < U; w0 += 32u * kUnits) {
         int4 v[kUnits];
         uint32_t lo[kUnits], ln[kUnits], e0[kUnits], rg[kUnits];
-        uint32_t ow[kUnits], pa[kUnits];
-        long long ep[kUnits];
         int qk[kUnits];
         bool in[kUnits];
 #pragma unroll
@@ -404,12 +401,7 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
             const uint32_t us = __shfl_sync(kFull, ustart, q);
             const uint32_t unit = wb + (uint32_t)lane;
             in[u] = unit < U;
-            if (EXTRA) {
-                ow[u] = __shfl_sync(kFull, r.owner, q);
-                pa[u] = __shfl_sync(kFull, r.partner, q);
-                ep[u] = __shfl_sync(kFull, epos, q);
-                qk[u] = in[u] ? q : 32 + lane;
-            }
+            if (EXTRA) qk[u] = q;
             e0[u] = (lo[u] & ~3u) + 4u * (unit - us);
             v[u] = in[u] ? __ldg(reinterpret_cast<const int4*>(a.cols + e0[u])) : make_int4(-1, -1, -1, -1);
         }
@@ -432,16 +424,40 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
                         if ((more >> k) & 1u) cnt += hash_probe_rest(hv, xs[k], (hash_start(hv, xs[k]) + 2) & hv.cmask) ? 1u : 0u;
                 }
             } else {
+                // per-vertex / per-edge: each hit counted at its slot, the unit's hits at its task
+                int sl[4];
+                uint32_t more;
+                find_batch<4>(hv, xs, ok, sl, more);
+                if (more) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if ((more >> k) & 1u) sl[k] = hash_find_rest(hv, xs[k], (hash_start(hv, xs[k]) + 2) & hv.cmask);
+                }
                 uint32_t h = 0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const bool hit = ok[k] && hash_probe(hv, xs[k]);
-                    h += hit ? 1u : 0u;
-                    if (hit && a.t_v) add_tv(a, xs[k]);
+                    if (sl[k] >= 0) {
+                        ++h;
+                        if (a.cnt_off) atomicAdd(hv.tbl + a.cnt_off + sl[k], 1u);
+                    }
                 }
                 cnt += h;
-                flush_task_hits(a, h, qk[u], ow[u], pa[u], ep[u], lane);
+                if (h) atomicAdd(&thits[qk[u]], h);
             }
+        }
+    }
+    if (EXTRA) {
+        // each task's hits to its owner, its partner and its oriented edge, once per batch
+        __syncwarp();
+        const uint32_t th = lane < na ? thits[lane] : 0u;
+        if (lane < na) thits[lane] = 0u;
+        __syncwarp();
+        if (th) {
+            if (a.t_v) {
+                atomicAdd(&a.t_v[r.owner], (unsigned long long)th);
+                atomicAdd(&a.t_v[r.partner], (unsigned long long)th);
+            }
+            if (a.per_edge) atomicAdd(&a.per_edge[oriented_edge_position(a, r.owner, r.partner)], th);
         }
     }
 }
@@ -552,6 +568,23 @@ __device__ void process_small(const CountArgs& a, long long t0, long long t1, ui
         __syncwarp();
         warp_batch<EXTRA, false>(a, r, nt, tbl, reg, 0u, 0xFFFFFFFFu, lane, acc);
         __syncwarp();
+        if (EXTRA && a.cnt_off) {
+            // the staged entries' hit counts to T_v, spread over the lanes as when they were staged
+            before = 0;
+            for (uint32_t base = 0; base < tot; base += 32u) {
+                const uint32_t rel = excl - base;
+                const uint32_t bit = (s_len != 0u && rel < 32u) ? (1u << rel) : 0u;
+                const uint32_t starts = __reduce_or_sync(kFull, bit);
+                const int q = ((int)(before + __popc(starts & lanemask_le())) - 1) & 31;
+                const long long obq = __shfl_sync(kFull, s_ob, q);
+                const uint32_t eq = __shfl_sync(kFull, excl, q);
+                const uint32_t rq = __shfl_sync(kFull, s_reg, q);
+                const uint32_t g = base + lane;
+                if (g < tot) flush_slot_hits(a, region_view(tbl, rq), obq + (g - eq), 1u, 0u, 1u);
+                before += __popc(starts);
+            }
+            __syncwarp();
+        }
         t += nt;
     }
 }
@@ -620,6 +653,10 @@ __device__ void big_owner_pieces(const CountArgs& a, long long t, long long tend
             warp_batch<EXTRA, true>(a, r, nb, tbl, reg, pmin, pmax, lane, acc);
         }
         __syncthreads();
+        if (EXTRA && a.cnt_off) {
+            flush_slot_hits(a, hv, ob + ps, pl, threadIdx.x, blockDim.x);
+            __syncthreads();
+        }
     }
 }
 
@@ -721,6 +758,11 @@ __device__ void process_big(const CountArgs& a, long long t0, long long t1, uint
                 warp_batch<EXTRA, true>(a, r, nb, tbl, reg, omin, omax, lane, acc);
             }
             __syncthreads();
+            if (EXTRA && a.cnt_off) {
+                for (int i = warp; i < nown; i += nwarps)
+                    flush_slot_hits(a, region_view(tbl, w->reg[i]), w->ob[i], w->ol[i], lane, 32u);
+                __syncthreads();  // before warp 0 rewrites the window record
+            }
         }
         t = tend;
         k += nown > 0 ? nown : 1;
@@ -840,6 +882,15 @@ __device__ __forceinline__ void worker_epilogue(const CountArgs& a, unsigned lon
     }
 }
 
+// Per-vertex / per-edge counts: zero the warps' task-hit counters and the slot counts (flushes
+// leave them zero again).  `slots`: the words of the block's tables.
+__device__ __forceinline__ void extra_init(const CountArgs& a, int slots) {
+    if (a.cnt_off)
+        for (int i = threadIdx.x; i < slots; i += blockDim.x) smem_dyn[a.cnt_off + i] = 0u;
+    for (int i = threadIdx.x; i < 32 * (int)(blockDim.x >> 5); i += blockDim.x) smem_dyn[a.hits_off + i] = 0u;
+    __syncthreads();
+}
+
 // Small owners: one worker per block, a table per warp.
 template <bool EXTRA>
 __global__ void __launch_bounds__(512, 2) k_count_small(CountArgs a) {
@@ -848,12 +899,11 @@ __global__ void __launch_bounds__(512, 2) k_count_small(CountArgs a) {
     uint32_t* tbl = smem_dyn + (size_t)warp * a.table_slots;
     unsigned long long acc = 0;
     long long busy = 0, nch = 0;
-    if (EXTRA) tv_cache_init(a);
+    if (EXTRA) extra_init(a, a.warps_per_block * a.table_slots);
     block_worker(a, [&](long long t0, long long t1) {
         by_graph<EXTRA>(a, t0, t1, [&](long long u0, long long u1) { process_small_block<EXTRA>(a, u0, u1, tbl, &s_claim, lane, acc); },
                  acc, lane, warp);
     }, lane, warp, busy, nch);
-    if (EXTRA) tv_cache_flush(a);
     worker_epilogue<EXTRA>(a, acc, lane, busy, nch);
 }
 
@@ -866,13 +916,12 @@ __global__ void __launch_bounds__(512, 2) k_count_big(CountArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long acc = 0;
     long long busy = 0, nch = 0;
-    if (EXTRA) tv_cache_init(a);
+    if (EXTRA) extra_init(a, a.table_slots);
     block_worker(a, [&](long long t0, long long t1) {
         by_graph<EXTRA>(a, t0, t1, [&](long long u0, long long u1) {
             process_big<EXTRA>(a, u0, u1, smem_tbl, &s_win, &s_next, lane, warp, acc);
         }, acc, lane, warp);
     }, lane, warp, busy, nch);
-    if (EXTRA) tv_cache_flush(a);
     worker_epilogue<EXTRA>(a, acc, lane, busy, nch);
 }
 
@@ -1034,18 +1083,22 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     TC_TRY(ensure_count_work(g, opt, s));
     CountWork& w = g->work;
     const long long T = g->tasks, Ts = g->tasks_small;
+    // Per-vertex counts keep a hit count beside every table slot, so their tables take twice the
+    // shared memory: they run with at most 8 warps per small-class block and pieces of at most
+    // 1024 entries (the block table of 8 * piece slots), which keeps two blocks per SM.
+    const int wpb = (t_v && opt.warps_per_block > 8) ? 8 : opt.warps_per_block;
+    const int piece = (t_v && opt.piece > 1024) ? 1024 : opt.piece;
+    const int tab = t_v ? 2 : 1;
     // small class: blocks whose warps each have a table
-    const int wpb = opt.warps_per_block;
     const int slots_s = small_table_slots(g->opt.small_max);
     const size_t smem_s = (size_t)wpb * slots_s * sizeof(uint32_t);
     // big class: blocks sharing one table of 8 * piece slots
     const int threads_b = opt.big_warps * 32;
-    const int slots_b = 8 * opt.piece;
+    const int slots_b = 8 * piece;
     const size_t smem_b = (size_t)slots_b * sizeof(uint32_t);
-    // per-vertex counts: a T_v cache of 2^kTvCacheLog (vertex, count) slots after the tables
-    const int cache_log = t_v ? kTvCacheLog : 0;
-    const size_t cache_bytes = cache_log ? ((size_t)2 << cache_log) * sizeof(uint32_t) : 0;
-    const size_t smem_s_x = smem_s + cache_bytes, smem_b_x = smem_b + cache_bytes;
+    // per-vertex / per-edge counts: slot counts after the tables, then 32 task-hit counters per warp
+    const size_t smem_s_x = smem_s * tab + (size_t)32 * wpb * sizeof(uint32_t);
+    const size_t smem_b_x = smem_b * tab + (size_t)32 * opt.big_warps * sizeof(uint32_t);
     int blocks_s = 0, blocks_b = 0;
     if (extra) {
         TC_TRY(grid_for_kernel(k_count_small<true>, wpb * 32, smem_s_x, opt.blocks_per_sm, &blocks_s));
@@ -1096,9 +1149,9 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     a.n_owners = g->owners_big;
     a.n_sub = g->n_sub;
     const bool count_streamed = trace && trace->count_streamed;
-    a.cache_log = cache_log;
     // small class
-    a.cache_off = wpb * slots_s;
+    a.cnt_off = t_v ? wpb * slots_s : 0;
+    a.hits_off = wpb * slots_s * tab;
     a.gtask = g->sub_task;
     a.streamed = count_streamed ? &w.sched[0].streamed : nullptr;
     a.t_begin = 0;
@@ -1106,7 +1159,7 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     a.sched = w.sched;
     a.W = W_s;
     a.cls = 0;
-    a.piece = opt.piece;
+    a.piece = piece;
     a.table_slots = slots_s;
     a.warps_per_block = wpb;
     a.busy_offset = 0;
@@ -1118,7 +1171,8 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     }
     if (trace) TC_CUDA_TRY(cudaEventRecord(ev[2], s));
     // big class
-    a.cache_off = slots_b;
+    a.cnt_off = t_v ? slots_b : 0;
+    a.hits_off = slots_b * tab;
     a.gtask = g->sub_task ? g->sub_task + (g->n_sub + 1) : nullptr;
     a.streamed = count_streamed ? &w.sched[1].streamed : nullptr;
     a.t_begin = Ts;
@@ -1250,8 +1304,8 @@ static tc_status count_enqueue_static(tc_graph* g, cudaStream_t s, unsigned long
     a.n_owners = g->owners_big;
     a.gtask = nullptr;
     a.streamed = nullptr;
-    a.cache_log = 0;
-    a.cache_off = 0;
+    a.cnt_off = 0;
+    a.hits_off = 0;
     a.n_sub = 0;
     a.t_begin = 0;
     a.t_end = Ts;
