@@ -1,7 +1,8 @@
 // batch.cu -- batched counting: many graphs packed into disjoint unions ("packs"), each pack
-// built by one pass of the single-graph pipeline and counted by one launch of each count
-// kernel; the counts of all packs are replayed from one captured CUDA graph.  The autotuner
-// times the batched count over a grid of hub thresholds and launch shapes.
+// built by one pass of the single-graph pipeline.  All packs are counted together: one cost
+// prefix over every pack's tasks, and per task class one schedule over the packs' concatenated
+// costs and one launch of the class kernel; that count is replayed from one captured CUDA
+// graph.  The autotuner times the batched count over a grid of hub thresholds and launch shapes.
 #include <algorithm>
 #include <chrono>
 #include <climits>
@@ -10,6 +11,7 @@
 #include <vector>
 
 #include "graph.cuh"
+#include "scan.cuh"
 
 namespace tcg {
 
@@ -90,6 +92,9 @@ struct tc_batch {
     Allocator al;                     // the batch's own buffers
     unsigned long long* totals = nullptr;  // device, k
     cudaStream_t cap_stream = nullptr;     // the stream captures are recorded on
+    PackDev* packs_dev = nullptr;          // device: one descriptor per pack
+    uint64_t* mscratch = nullptr;          // device: the multi-pack count's bases, schedule and scan scratch
+    int64_t mscratch_words = 0;
     cudaGraphExec_t exec = nullptr;
     int kernels_per_run = 0;               // kernel nodes in the captured graph
     cudaStream_t last_stream = nullptr;
@@ -106,6 +111,8 @@ static void destroy_batch(tc_batch* b) {
     if (!b) return;
     cudaStreamSynchronize(b->last_stream);
     drop_capture(b);
+    if (b->packs_dev) b->al.put(b->packs_dev, b->packs.size() * sizeof(PackDev), b->last_stream);
+    if (b->mscratch) b->al.put(b->mscratch, (size_t)b->mscratch_words * 8, b->last_stream);
     for (tc_graph* g : b->packs) free_graph(g);
     if (b->totals) b->al.put(b->totals, (size_t)(b->k > 0 ? b->k : 1) * 8, b->last_stream);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -213,17 +220,54 @@ static tc_status build_pack(const int32_t* const* src, const int32_t* const* dst
     return TC_OK;
 }
 
-// Record the counts of every pack into one CUDA graph (work buffers allocated beforehand).
+// Record the count of every pack into one CUDA graph (work buffers and the pack descriptors
+// set up beforehand).
 static tc_status capture_batch(tc_batch* b) {
     drop_capture(b);
-    for (tc_graph* g : b->packs) TC_TRY(ensure_count_work(g, b->opt, b->cap_stream));
+    const size_t np = b->packs.size();
+    int64_t total_tasks = 0, tiles = 0;
+    std::vector<PackDev> hp(np);
+    for (size_t p = 0; p < np; ++p) {
+        tc_graph* g = b->packs[p];
+        TC_TRY(ensure_count_work(g, b->opt, b->cap_stream));
+        PackDev& d = hp[p];
+        d.off = g->off;
+        d.cols = g->cols;
+        d.tasks = g->trec;
+        d.deg = g->deg;
+        d.P = g->work.prefix;
+        d.fcost = g->work.fcost;
+        d.own_first = g->own_first;
+        d.n_owners = g->owners_big;
+        d.sub_task = g->sub_task;
+        d.n_sub = g->n_sub;
+        d.Ts = g->tasks_small;
+        d.T = g->tasks;
+        d.task_base = total_tasks;
+        d.tile_base = tiles;  // each pack's cost prefix starts a new scan tile
+        d.total = b->totals + b->first[p];
+        total_tasks += g->tasks;
+        tiles += ceil_div(g->tasks, kScanTile);
+    }
+    if (!b->packs_dev && np > 0) {
+        void* q = nullptr;
+        TC_TRY(b->al.get(&q, np * sizeof(PackDev), b->cap_stream));
+        b->packs_dev = (PackDev*)q;
+    }
+    if (!b->mscratch && np > 0) {
+        void* q = nullptr;
+        b->mscratch_words = multi_scratch_words(total_tasks, (int)np);
+        TC_TRY(b->al.get(&q, (size_t)b->mscratch_words * 8, b->cap_stream));
+        b->mscratch = (uint64_t*)q;
+    }
+    if (np > 0)
+        TC_CUDA_TRY(cudaMemcpyAsync(b->packs_dev, hp.data(), np * sizeof(PackDev), cudaMemcpyHostToDevice, b->cap_stream));
     TC_CUDA_TRY(cudaStreamSynchronize(b->cap_stream));
     TC_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     tc_status st = TC_OK;
     // kernels are counted when they run, not when they are recorded
     const int64_t l0 = tc_kernel_launches();
-    for (size_t p = 0; p < b->packs.size() && st == TC_OK; ++p)
-        st = count_enqueue(b->packs[p], b->opt, b->cap_stream, b->totals + b->first[p], nullptr, nullptr, nullptr);
+    st = count_enqueue_multi(b->packs, b->packs_dev, b->mscratch, b->opt, b->totals, b->k, b->cap_stream);
     b->kernels_per_run = (int)(tc_kernel_launches() - l0);
     note_launch(-b->kernels_per_run);
     cudaGraph_t graph = nullptr;

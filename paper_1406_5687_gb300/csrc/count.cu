@@ -71,6 +71,13 @@ struct CountArgs {
     int cnt_off;                   // per-vertex counts: words from a table slot to its hit count (0: none)
     int hits_off;                  // per-vertex / per-edge counts: the warps' task-hit counters, in words
     long long n_sub;            // packs: graphs (0: one graph, one total)
+    // multi-pack counts (a batch's packs in one launch): the packs, and per class each pack's
+    // first task in the class's concatenated order (then the end) and the class cost before it
+    // (then the total)
+    const PackDev* packs;
+    int n_packs;
+    const long long* tbase;
+    const unsigned long long* cbase;
 };
 
 // First index q in [lo, hi] with pred(q), for pred false..false true..true and pred(hi) true.
@@ -107,6 +114,76 @@ __device__ __forceinline__ long long class_bound(const CountArgs& a, unsigned lo
     const uint64_t* __restrict__ P = a.P;
     const unsigned long long target = x + base;
     return warp_first_true(a.t_begin, a.t_end, [&](long long q) { return P[q] >= target; }, lane);
+}
+
+// Multi-pack counts: cost boundary x of the class (counted over the packs one after another)
+// -> the first task, in the class's concatenated order, whose exclusive prefix reaches x.
+__device__ __forceinline__ long long class_bound_multi(const CountArgs& a, unsigned long long x, unsigned long long C,
+                                                       int lane) {
+    const int np = a.n_packs;
+    if (x >= C) return a.tbase[np];
+    // the pack holding cost x: the first whose end lies beyond x
+    const unsigned long long* __restrict__ cb = a.cbase;
+    const long long p = warp_first_true(0, np - 1, [&](long long q) { return cb[q + 1] > x; }, lane);
+    const PackDev& pk = a.packs[p];
+    const long long lb = a.cls == 0 ? 0 : pk.Ts, ub = a.cls == 0 ? pk.Ts : pk.T;
+    const uint64_t* __restrict__ P = pk.P;
+    const unsigned long long target = P[lb] + (x - cb[p]);
+    const long long j = warp_first_true(lb, ub, [&](long long q) { return P[q] >= target; }, lane);
+    return a.tbase[p] + (j - lb);
+}
+
+// Multi-pack counts: call fn(b, l0, l1) for every pack piece of the class's tasks [g0, g1)
+// (concatenated order), b the arguments of that pack and [l0, l1) its local tasks.  Every
+// thread of the block calls this.  Warp 0 prepares each piece in shared memory (the pack's
+// arguments in one copy the block shares, the piece's bounds, where the next piece starts),
+// so that no loop state stays live in registers while the block counts a piece.
+template <class Fn>
+__device__ __forceinline__ void for_pack_pieces(const CountArgs& a, long long g0, long long g1, int lane, Fn fn) {
+    __shared__ CountArgs s_b;
+    __shared__ long long s_piece[3];  // local first and end task, then where the next piece starts
+    if (threadIdx.x == 0) s_piece[2] = g0;
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x < 32) {
+            const long long g = s_piece[2];
+            long long e = g;
+            if (g < g1) {
+                // the pack of g: the first whose end lies beyond g (packs without tasks skipped)
+                const long long* __restrict__ tb = a.tbase;
+                const int np = a.n_packs;
+                const long long p = warp_first_true(0, np - 1, [&](long long q) { return tb[q + 1] > g; }, lane);
+                e = tb[p + 1] < g1 ? tb[p + 1] : g1;
+                if (lane == 0) {
+                    const PackDev& pk = a.packs[p];
+                    s_b = a;
+                    s_b.off = pk.off;
+                    s_b.cols = pk.cols;
+                    s_b.tasks = pk.tasks;
+                    s_b.deg = pk.deg;
+                    s_b.P = pk.P;
+                    s_b.own_first = pk.own_first;
+                    s_b.n_owners = pk.n_owners;
+                    s_b.n_sub = pk.n_sub;
+                    s_b.gtask = pk.sub_task + (a.cls == 0 ? 0 : pk.n_sub + 1);
+                    s_b.total = pk.total;
+                    s_b.t_begin = a.cls == 0 ? 0 : pk.Ts;
+                    s_b.t_end = a.cls == 0 ? pk.Ts : pk.T;
+                    s_piece[0] = s_b.t_begin + (g - tb[p]);
+                    s_piece[1] = s_b.t_begin + (e - tb[p]);
+                }
+            }
+            if (lane == 0) s_piece[2] = e == g ? g1 : e;  // nothing left (g >= g1): stop
+            if (lane == 0 && e == g) s_piece[0] = s_piece[1] = 0;
+        }
+        __syncthreads();
+        // read before the barrier below: warp 0 rewrites the piece words after it
+        const long long l0 = s_piece[0], l1 = s_piece[1];
+        const bool last = s_piece[2] >= g1;
+        if (l1 > l0) fn(s_b, l0, l1);
+        __syncthreads();  // every thread is done with this piece's arguments
+        if (last) break;
+    }
 }
 
 // Position of u in the sorted list N+(v).
@@ -772,7 +849,7 @@ __device__ void process_big(const CountArgs& a, long long t0, long long t1, uint
 // Scheduling loop of one block-wide worker (Sec. V-B): its Eq. 1 initial chunk, then Eq. 2
 // chunks popped by thread 0 until the class's cost is exhausted.  `process(t0, t1)` is
 // called by every thread of the block.
-template <class Process>
+template <bool MULTI, class Process>
 __device__ __forceinline__ void block_worker(const CountArgs& a, Process process, int lane, int warp,
                                              long long& busy, long long& nch) {
     __shared__ long long s_t[2];
@@ -792,13 +869,15 @@ __device__ __forceinline__ void block_worker(const CountArgs& a, Process process
         long long t0;
         if (wid == 0 && a.sched->at_start) {
             t0 = a.t_begin;
+        } else if (MULTI) {
+            t0 = class_bound_multi(a, lo, C, lane);
         } else if (wid == 0) {
             const uint64_t* __restrict__ P = a.P;
             t0 = warp_first_true(a.t_begin, a.t_end, [&](long long q) { return P[q] >= base; }, lane);
         } else {
             t0 = class_bound(a, lo, C, base, lane);
         }
-        const long long t1 = class_bound(a, hi, C, base, lane);
+        const long long t1 = MULTI ? class_bound_multi(a, hi, C, lane) : class_bound(a, hi, C, base, lane);
         if (lane == 0) {
             s_t[0] = t0;
             s_t[1] = t1;
@@ -822,8 +901,8 @@ __device__ __forceinline__ void block_worker(const CountArgs& a, Process process
         __syncthreads();
         if (!s_got) break;
         if (warp == 0) {
-            const long long t0 = class_bound(a, s_c[0], C, base, lane);
-            const long long t1 = class_bound(a, s_c[1], C, base, lane);
+            const long long t0 = MULTI ? class_bound_multi(a, s_c[0], C, lane) : class_bound(a, s_c[0], C, base, lane);
+            const long long t1 = MULTI ? class_bound_multi(a, s_c[1], C, lane) : class_bound(a, s_c[1], C, base, lane);
             if (lane == 0) {
                 s_t[0] = t0;
                 s_t[1] = t1;
@@ -891,8 +970,8 @@ __device__ __forceinline__ void extra_init(const CountArgs& a, int slots) {
     __syncthreads();
 }
 
-// Small owners: one worker per block, a table per warp.
-template <bool EXTRA>
+// Small owners: one worker per block, a table per warp.  MULTI: the packs of a batch.
+template <bool EXTRA, bool MULTI>
 __global__ void __launch_bounds__(512, 2) k_count_small(CountArgs a) {
     __shared__ unsigned s_claim;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -900,15 +979,25 @@ __global__ void __launch_bounds__(512, 2) k_count_small(CountArgs a) {
     unsigned long long acc = 0;
     long long busy = 0, nch = 0;
     if (EXTRA) extra_init(a, a.warps_per_block * a.table_slots);
-    block_worker(a, [&](long long t0, long long t1) {
-        by_graph<EXTRA>(a, t0, t1, [&](long long u0, long long u1) { process_small_block<EXTRA>(a, u0, u1, tbl, &s_claim, lane, acc); },
-                 acc, lane, warp);
-    }, lane, warp, busy, nch);
+    if (MULTI) {
+        block_worker<true>(a, [&](long long g0, long long g1) {
+            for_pack_pieces(a, g0, g1, lane, [&](const CountArgs& b, long long l0, long long l1) {
+                by_graph<false>(b, l0, l1, [&](long long u0, long long u1) {
+                    process_small_block<false>(b, u0, u1, tbl, &s_claim, lane, acc);
+                }, acc, lane, warp);
+            });
+        }, lane, warp, busy, nch);
+    } else {
+        block_worker<false>(a, [&](long long t0, long long t1) {
+            by_graph<EXTRA>(a, t0, t1, [&](long long u0, long long u1) { process_small_block<EXTRA>(a, u0, u1, tbl, &s_claim, lane, acc); },
+                     acc, lane, warp);
+        }, lane, warp, busy, nch);
+    }
     worker_epilogue<EXTRA>(a, acc, lane, busy, nch);
 }
 
-// Big owners: one worker per block, one table per block.
-template <bool EXTRA>
+// Big owners: one worker per block, one table per block.  MULTI: the packs of a batch.
+template <bool EXTRA, bool MULTI>
 __global__ void __launch_bounds__(512, 2) k_count_big(CountArgs a) {
     uint32_t* smem_tbl = smem_dyn;
     __shared__ BigWindow s_win;
@@ -917,11 +1006,21 @@ __global__ void __launch_bounds__(512, 2) k_count_big(CountArgs a) {
     unsigned long long acc = 0;
     long long busy = 0, nch = 0;
     if (EXTRA) extra_init(a, a.table_slots);
-    block_worker(a, [&](long long t0, long long t1) {
-        by_graph<EXTRA>(a, t0, t1, [&](long long u0, long long u1) {
-            process_big<EXTRA>(a, u0, u1, smem_tbl, &s_win, &s_next, lane, warp, acc);
-        }, acc, lane, warp);
-    }, lane, warp, busy, nch);
+    if (MULTI) {
+        block_worker<true>(a, [&](long long g0, long long g1) {
+            for_pack_pieces(a, g0, g1, lane, [&](const CountArgs& b, long long l0, long long l1) {
+                by_graph<false>(b, l0, l1, [&](long long u0, long long u1) {
+                    process_big<false>(b, u0, u1, smem_tbl, &s_win, &s_next, lane, warp, acc);
+                }, acc, lane, warp);
+            });
+        }, lane, warp, busy, nch);
+    } else {
+        block_worker<false>(a, [&](long long t0, long long t1) {
+            by_graph<EXTRA>(a, t0, t1, [&](long long u0, long long u1) {
+                process_big<EXTRA>(a, u0, u1, smem_tbl, &s_win, &s_next, lane, warp, acc);
+            }, acc, lane, warp);
+        }, lane, warp, busy, nch);
+    }
     worker_epilogue<EXTRA>(a, acc, lane, busy, nch);
 }
 
@@ -1101,11 +1200,11 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     const size_t smem_b_x = smem_b * tab + (size_t)32 * opt.big_warps * sizeof(uint32_t);
     int blocks_s = 0, blocks_b = 0;
     if (extra) {
-        TC_TRY(grid_for_kernel(k_count_small<true>, wpb * 32, smem_s_x, opt.blocks_per_sm, &blocks_s));
-        TC_TRY(grid_for_kernel(k_count_big<true>, threads_b, smem_b_x, opt.blocks_per_sm, &blocks_b));
+        TC_TRY(grid_for_kernel(k_count_small<true, false>, wpb * 32, smem_s_x, opt.blocks_per_sm, &blocks_s));
+        TC_TRY(grid_for_kernel(k_count_big<true, false>, threads_b, smem_b_x, opt.blocks_per_sm, &blocks_b));
     } else {
-        TC_TRY(grid_for_kernel(k_count_small<false>, wpb * 32, smem_s, opt.blocks_per_sm, &blocks_s));
-        TC_TRY(grid_for_kernel(k_count_big<false>, threads_b, smem_b, opt.blocks_per_sm, &blocks_b));
+        TC_TRY(grid_for_kernel(k_count_small<false, false>, wpb * 32, smem_s, opt.blocks_per_sm, &blocks_s));
+        TC_TRY(grid_for_kernel(k_count_big<false, false>, threads_b, smem_b, opt.blocks_per_sm, &blocks_b));
     }
     const long long W_s = blocks_s, W_b = blocks_b;  // one worker per block in both classes
 
@@ -1149,6 +1248,10 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     a.n_owners = g->owners_big;
     a.n_sub = g->n_sub;
     const bool count_streamed = trace && trace->count_streamed;
+    a.packs = nullptr;
+    a.n_packs = 0;
+    a.tbase = nullptr;
+    a.cbase = nullptr;
     // small class
     a.cnt_off = t_v ? wpb * slots_s : 0;
     a.hits_off = wpb * slots_s * tab;
@@ -1164,8 +1267,8 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     a.warps_per_block = wpb;
     a.busy_offset = 0;
     if (Ts > 0) {
-        if (extra) k_count_small<true><<<blocks_s, wpb * 32, smem_s_x, s>>>(a);
-        else k_count_small<false><<<blocks_s, wpb * 32, smem_s, s>>>(a);
+        if (extra) k_count_small<true, false><<<blocks_s, wpb * 32, smem_s_x, s>>>(a);
+        else k_count_small<false, false><<<blocks_s, wpb * 32, smem_s, s>>>(a);
         note_launch();
         TC_CUDA_TRY(cudaGetLastError());
     }
@@ -1184,8 +1287,8 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
     a.warps_per_block = opt.big_warps;
     a.busy_offset = W_s;
     if (T > Ts) {
-        if (extra) k_count_big<true><<<blocks_b, threads_b, smem_b_x, s>>>(a);
-        else k_count_big<false><<<blocks_b, threads_b, smem_b, s>>>(a);
+        if (extra) k_count_big<true, false><<<blocks_b, threads_b, smem_b_x, s>>>(a);
+        else k_count_big<false, false><<<blocks_b, threads_b, smem_b, s>>>(a);
         note_launch();
         TC_CUDA_TRY(cudaGetLastError());
     }
@@ -1211,6 +1314,278 @@ tc_status count_enqueue(tc_graph* g, const tc_options& opt, cudaStream_t s, unsi
         TC_CUDA_TRY(cudaEventElapsedTime(&ms, ev[2], ev[3]));
         trace->kernel_big_ms = ms;
         for (auto& e : ev) cudaEventDestroy(e);
+    }
+    return TC_OK;
+}
+
+// --------------------------------------------------------------------------- multi-pack count
+//
+// A batch's packs counted together: one cost prefix over all packs' tasks (pack after pack),
+// then per class one schedule over the packs' concatenated costs and one launch of the class
+// kernel, whose workers count each chunk pack piece by pack piece.
+
+// The multi-pack cost prefix.  Each pack's tasks start a new scan tile, so every tile lies in
+// one pack: a block finds its pack once and evaluates that pack's task costs.  Tile sums, a
+// scan of them (scan_exclusive), the downsweep into each pack's P, and each pack's end value
+// P[T] = the prefix at the start of the next pack's first tile.
+__device__ __forceinline__ int pack_of_tile(const PackDev* __restrict__ packs, int np, long long tile) {
+    int lo = 0, hi = np - 1;  // the last pack whose first tile is at or before `tile`
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (packs[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct MultiCostArgs {
+    const PackDev* packs;
+    int np;
+    int model;
+    uint32_t piece, small_max, c_task, c_owner;
+};
+
+__device__ __forceinline__ TaskCost block_pack_cost(const MultiCostArgs& m, const PackDev*& pk, int64_t& first) {
+    __shared__ int s_p;
+    if (threadIdx.x == 0) s_p = pack_of_tile(m.packs, m.np, (long long)blockIdx.x);
+    __syncthreads();
+    pk = m.packs + s_p;
+    first = (int64_t)(blockIdx.x - pk->tile_base) * kScanTile;  // the block's first task in its pack
+    return TaskCost{pk->tasks, pk->T, pk->off, pk->fcost, m.model, m.piece, m.small_max, m.c_task, m.c_owner};
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_multi_tile_sums(MultiCostArgs m, uint64_t* tile_sums) {
+    const PackDev* pk;
+    int64_t first;
+    const TaskCost f = block_pack_cost(m, pk, first);
+    const int64_t n = pk->T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = first + (int64_t)warp * 32 * kScanItems;
+    uint64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + k * 32 + lane;
+        if (i < n) s += f(i);
+    }
+    s = warp_sum(s);
+    __shared__ uint64_t ws[kScanBlock / 32];
+    if (lane == 0) ws[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t t = 0;
+        for (int w = 0; w < kScanBlock / 32; ++w) t += ws[w];
+        tile_sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_multi_downsweep(MultiCostArgs m, const uint64_t* tile_prefix) {
+    const PackDev* pk;
+    int64_t first;
+    const TaskCost f = block_pack_cost(m, pk, first);
+    const int64_t n = pk->T;
+    uint64_t* __restrict__ out = pk->P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = first + (int64_t)warp * 32 * kScanItems;
+    uint64_t ex[kScanItems];
+    uint64_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + k * 32 + lane;
+        const uint64_t v = i < n ? f(i) : 0;
+        const uint64_t incl = warp_inclusive_scan(v, lane);
+        ex[k] = carry + incl - v;
+        carry += __shfl_sync(kFull, incl, 31);
+    }
+    __shared__ uint64_t ws[kScanBlock / 32];
+    if (lane == 0) ws[warp] = carry;
+    __syncthreads();
+    uint64_t woff = tile_prefix[blockIdx.x];
+    for (int w = 0; w < warp; ++w) woff += ws[w];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + k * 32 + lane;
+        if (i < n) out[i] = woff + ex[k];
+    }
+}
+
+// P[T] of every pack: the prefix at the start of the next pack's first tile (the last pack: the
+// total).  Padding past a pack's last task costs nothing, so that is the sum through the pack.
+__global__ void k_multi_pack_ends(const PackDev* packs, int np, long long tiles, const uint64_t* tile_prefix) {
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        const PackDev& pk = packs[p];
+        if (pk.T == 0) continue;
+        const long long next = p + 1 < np ? packs[p + 1].tile_base : tiles;
+        pk.P[pk.T] = tile_prefix[next];
+    }
+}
+
+// Per class: each pack's first task and cost base in the class's concatenated order, and the
+// class's schedule (Eq. 1 share and Eq. 2 floor over the total, as k_sched_init).
+__global__ void k_multi_sched_init(const PackDev* packs, int np, long long* tb0, long long* tb1, unsigned long long* cb0,
+                                   unsigned long long* cb1, Sched* sc, long long W0, long long W1, int static_percent,
+                                   long long min_chunk) {
+    long long t0 = 0, t1 = 0;
+    unsigned long long c0 = 0, c1 = 0;
+    for (int p = 0; p < np; ++p) {
+        tb0[p] = t0;
+        tb1[p] = t1;
+        cb0[p] = c0;
+        cb1[p] = c1;
+        const PackDev& pk = packs[p];
+        if (pk.T > 0) {
+            c0 += pk.P[pk.Ts] - pk.P[0];
+            c1 += pk.P[pk.T] - pk.P[pk.Ts];
+        }
+        t0 += pk.Ts;
+        t1 += pk.T - pk.Ts;
+    }
+    tb0[np] = t0;
+    tb1[np] = t1;
+    cb0[np] = c0;
+    cb1[np] = c1;
+    const unsigned long long sp = (unsigned long long)static_percent;
+    for (int c = 0; c < 2; ++c) {
+        const unsigned long long C = c == 0 ? c0 : c1;
+        const unsigned long long W = (unsigned long long)(c == 0 ? W0 : W1);
+        unsigned long long minc = (unsigned long long)min_chunk;
+        if (min_chunk <= 0) {
+            minc = C / (W * 128ull);
+            if (minc < 32ull) minc = 32ull;
+        }
+        sc[c].C = C;
+        sc[c].H = (C / 100ull) * sp + ((C % 100ull) * sp) / 100ull;
+        sc[c].min_chunk = minc;
+        sc[c].head = sc[c].H;
+        sc[c].n_chunks = 0;
+        sc[c].base = 0;
+        sc[c].streamed = 0;
+        sc[c].at_start = 1;
+        sc[c].at_end = 1;
+    }
+}
+
+static int64_t multi_fixed_words(int n_packs) {
+    return 4 * ((int64_t)n_packs + 1) + (int64_t)((2 * sizeof(Sched) + 7) / 8);
+}
+
+int64_t multi_scratch_words(int64_t total_tasks, int n_packs) {
+    // each pack starts a new scan tile: at most n_packs tiles more than the tasks need
+    return multi_fixed_words(n_packs) + scan_scratch_words(total_tasks + (int64_t)n_packs * kScanTile);
+}
+
+tc_status count_enqueue_multi(const std::vector<tc_graph*>& packs, const PackDev* packs_dev, uint64_t* scratch,
+                              const tc_options& opt, unsigned long long* totals, int32_t k, cudaStream_t s) {
+    const int np = (int)packs.size();
+    if (np == 0) return TC_OK;
+    int64_t total_tasks = 0, small_tasks = 0;
+    for (tc_graph* g : packs) {
+        total_tasks += g->tasks;
+        small_tasks += g->tasks_small;
+    }
+    long long* tb0 = reinterpret_cast<long long*>(scratch);
+    long long* tb1 = tb0 + np + 1;
+    unsigned long long* cb0 = reinterpret_cast<unsigned long long*>(tb1 + np + 1);
+    unsigned long long* cb1 = cb0 + np + 1;
+    Sched* sc = reinterpret_cast<Sched*>(cb1 + np + 1);
+    uint64_t* scan_scr = scratch + multi_fixed_words(np);
+
+    const int wpb = opt.warps_per_block;
+    const int slots_s = small_table_slots(packs[0]->opt.small_max);
+    const size_t smem_s = (size_t)wpb * slots_s * sizeof(uint32_t);
+    const int threads_b = opt.big_warps * 32;
+    const int slots_b = 8 * opt.piece;
+    const size_t smem_b = (size_t)slots_b * sizeof(uint32_t);
+    int blocks_s = 0, blocks_b = 0;
+    TC_TRY(grid_for_kernel(k_count_small<false, true>, wpb * 32, smem_s, opt.blocks_per_sm, &blocks_s));
+    TC_TRY(grid_for_kernel(k_count_big<false, true>, threads_b, smem_b, opt.blocks_per_sm, &blocks_b));
+
+    // a6 over every pack at once
+    if (opt.cost_model >= TC_COST_ONE) {
+        const int fn = opt.cost_model - TC_COST_ONE;
+        for (tc_graph* g : packs) TC_TRY(vertex_cost_enqueue(g, fn, s, g->work.fcost));
+    }
+    if (total_tasks > 0) {
+        long long tiles = 0;
+        for (tc_graph* g : packs) tiles += ceil_div(g->tasks, kScanTile);
+        const MultiCostArgs m{packs_dev, np, opt.cost_model, (uint32_t)opt.piece, (uint32_t)packs[0]->opt.small_max,
+                              (uint32_t)opt.c_task, (uint32_t)opt.c_owner};
+        uint64_t* tile = scan_scr;  // tiles + 1
+        k_multi_tile_sums<<<(unsigned)tiles, kScanBlock, 0, s>>>(m, tile);
+        note_launch();
+        if (tiles <= 4096) {
+            k_scan_single_block<<<1, 1024, 0, s>>>(tile, tiles);
+            note_launch();
+        } else {
+            uint64_t* tmp = scan_scr + tiles + 1;
+            TC_CUDA_TRY(scan_exclusive(IdentityU64{tile}, tiles, tmp, tmp + tiles + 1, s));
+            TC_CUDA_TRY(cudaMemcpyAsync(tile, tmp, (tiles + 1) * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        }
+        k_multi_downsweep<<<(unsigned)tiles, kScanBlock, 0, s>>>(m, tile);
+        note_launch();
+        k_multi_pack_ends<<<1, 256, 0, s>>>(packs_dev, np, tiles, tile);
+        note_launch();
+        TC_CUDA_TRY(cudaGetLastError());
+    }
+    k_multi_sched_init<<<1, 1, 0, s>>>(packs_dev, np, tb0, tb1, cb0, cb1, sc, blocks_s, blocks_b, opt.static_percent,
+                                       opt.min_chunk);
+    note_launch();
+    TC_CUDA_TRY(cudaGetLastError());
+    TC_CUDA_TRY(cudaMemsetAsync(totals, 0, sizeof(unsigned long long) * (k > 0 ? k : 1), s));
+
+    CountArgs a;
+    a.off = nullptr;
+    a.cols = nullptr;
+    a.tasks = nullptr;
+    a.deg = nullptr;
+    a.P = nullptr;
+    a.trace_sched = sc;
+    a.total = totals;
+    a.t_v = nullptr;
+    a.per_edge = nullptr;
+    a.trace_chunks = nullptr;
+    a.trace_cap = 0;
+    a.trace_busy = nullptr;
+    a.busy_offset = 0;
+    a.status = packs[0]->status;
+    a.retry_limit = opt.retry_limit > 0 ? opt.retry_limit : (1ll << 24);
+    a.own_first = nullptr;
+    a.n_owners = 0;
+    a.gtask = nullptr;
+    a.n_sub = 0;
+    a.streamed = nullptr;
+    a.cnt_off = 0;
+    a.hits_off = 0;
+    a.packs = packs_dev;
+    a.n_packs = np;
+    a.piece = opt.piece;
+    // small class
+    a.tbase = tb0;
+    a.cbase = cb0;
+    a.t_begin = 0;
+    a.t_end = small_tasks;
+    a.sched = sc;
+    a.W = blocks_s;
+    a.cls = 0;
+    a.table_slots = slots_s;
+    a.warps_per_block = wpb;
+    if (small_tasks > 0) {
+        k_count_small<false, true><<<blocks_s, wpb * 32, smem_s, s>>>(a);
+        note_launch();
+        TC_CUDA_TRY(cudaGetLastError());
+    }
+    // big class
+    a.tbase = tb1;
+    a.cbase = cb1;
+    a.t_begin = 0;
+    a.t_end = total_tasks - small_tasks;
+    a.sched = sc + 1;
+    a.W = blocks_b;
+    a.cls = 1;
+    a.table_slots = slots_b;
+    a.warps_per_block = opt.big_warps;
+    if (total_tasks > small_tasks) {
+        k_count_big<false, true><<<blocks_b, threads_b, smem_b, s>>>(a);
+        note_launch();
+        TC_CUDA_TRY(cudaGetLastError());
     }
     return TC_OK;
 }
@@ -1273,8 +1648,8 @@ static tc_status count_enqueue_static(tc_graph* g, cudaStream_t s, unsigned long
     const int slots_b = 8 * opt.piece;
     const size_t smem_b = (size_t)slots_b * sizeof(uint32_t);
     int blocks_s = 0, blocks_b = 0;
-    TC_TRY(grid_for_kernel(k_count_small<false>, wpb * 32, smem_s, opt.blocks_per_sm, &blocks_s));
-    TC_TRY(grid_for_kernel(k_count_big<false>, threads_b, smem_b, opt.blocks_per_sm, &blocks_b));
+    TC_TRY(grid_for_kernel(k_count_small<false, false>, wpb * 32, smem_s, opt.blocks_per_sm, &blocks_s));
+    TC_TRY(grid_for_kernel(k_count_big<false, false>, threads_b, smem_b, opt.blocks_per_sm, &blocks_b));
     const long long W_s = blocks_s, W_b = blocks_b;
 
     TaskCost tcf{g->trec, T, g->off, nullptr, opt.cost_model, (uint32_t)opt.piece, (uint32_t)opt.small_max,
@@ -1306,6 +1681,10 @@ static tc_status count_enqueue_static(tc_graph* g, cudaStream_t s, unsigned long
     a.streamed = nullptr;
     a.cnt_off = 0;
     a.hits_off = 0;
+    a.packs = nullptr;
+    a.n_packs = 0;
+    a.tbase = nullptr;
+    a.cbase = nullptr;
     a.n_sub = 0;
     a.t_begin = 0;
     a.t_end = Ts;
@@ -1317,7 +1696,7 @@ static tc_status count_enqueue_static(tc_graph* g, cudaStream_t s, unsigned long
     a.warps_per_block = wpb;
     a.busy_offset = 0;
     if (Ts > 0) {
-        k_count_small<false><<<blocks_s, wpb * 32, smem_s, s>>>(a);
+        k_count_small<false, false><<<blocks_s, wpb * 32, smem_s, s>>>(a);
         note_launch();
         TC_CUDA_TRY(cudaGetLastError());
     }
@@ -1330,7 +1709,7 @@ static tc_status count_enqueue_static(tc_graph* g, cudaStream_t s, unsigned long
     a.warps_per_block = opt.big_warps;
     a.busy_offset = W_s;
     if (T > Ts) {
-        k_count_big<false><<<blocks_b, threads_b, smem_b, s>>>(a);
+        k_count_big<false, false><<<blocks_b, threads_b, smem_b, s>>>(a);
         note_launch();
         TC_CUDA_TRY(cudaGetLastError());
     }

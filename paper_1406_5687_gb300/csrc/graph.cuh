@@ -101,6 +101,34 @@ tc_status vertex_cost_enqueue(tc_graph* g, int fn, cudaStream_t s, uint64_t* f);
 
 tc_status clustering_enqueue(tc_graph* g, const uint64_t* t_v, double* cc, cudaStream_t s);
 
+// One pack of a batch as the multi-pack count sees it (device memory, one per pack).  A pack's
+// cost prefix P holds running sums over the whole batch (pack after pack); only differences
+// within a pack are used.
+struct PackDev {
+    const int64_t* off;
+    const int32_t* cols;
+    const TaskRec* tasks;
+    const int32_t* deg;
+    uint64_t* P;                 // T + 1
+    const uint64_t* fcost;       // per-vertex cost models only
+    const uint32_t* own_first;
+    long long n_owners;
+    const int64_t* sub_task;     // per class: first task of each graph, then the class end
+    long long n_sub;
+    long long Ts, T;
+    long long task_base;         // first task of this pack in the batch's pack-after-pack order
+    long long tile_base;         // first scan tile of this pack (each pack starts a new tile)
+    unsigned long long* total;   // the totals of the pack's graphs
+};
+
+// Count every pack of a batch with one cost prefix over all packs and one launch of each
+// class kernel: per class, one Eq. 1 + Eq. 2 schedule over the packs' concatenated costs.
+// `packs_dev`: n_packs PackDev entries (device), followed by scratch the call lays out itself
+// (multi_scratch_words(...) uint64 words at `scratch`).  totals: device, the batch's k totals.
+int64_t multi_scratch_words(int64_t total_tasks, int n_packs);
+tc_status count_enqueue_multi(const std::vector<tc_graph*>& packs, const PackDev* packs_dev, uint64_t* scratch,
+                              const tc_options& opt, unsigned long long* totals, int32_t k, cudaStream_t s);
+
 // Build (build.cu).  src/dst are device pointers here.
 tc_status build_graph(tc_graph* g, const int32_t* src_d, const int32_t* dst_d, int64_t m, int32_t n,
                       cudaStream_t s);
