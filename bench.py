@@ -651,6 +651,29 @@ def surrogate_leg(s_dev, d_dev, n, opt, T_ref, stream, fraction=4, reps=3):
         return {"ms": best, "value": m / (best / 1e3), "unit": UNIT}
 
     host = timed(off_h, cols_h, cuts)
+    # cuts bounded in work (Sec. IV-F cost, as many parts) and in size (the same byte bound) at once:
+    # parts of more even time, for ranks that count parts side by side
+    both = tc.surrogate_plan_both(off_h, cols_h, len(cuts) - 1, budget)
+    host_both = timed(off_h, cols_h, both)
+
+    def part_times(cu):
+        # each receiving part alone (its messages routed and counted), best of 2, CUDA events
+        out = []
+        for j in range(len(cu) - 1):
+            best = None
+            for _ in range(2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                tc.count_surrogate(off_h, cols_h, cu, part_lo=j, part_hi=j + 1, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None or ms < best else best
+            out.append(best)
+        return {"part_ms": out, "max_over_mean": max(out) / (sum(out) / len(out))}
+
+    parts_equal, parts_both = part_times(cuts), part_times(both)
+    bs = o[both[1:]] - o[both[:-1]]
     # one more call with the work counters and per-kernel CUDA events (outside the timed best-of)
     T, _tab, st = tc.count_surrogate(off_h, cols_h, cuts, stream=stream, stats=True)
     if T != T_ref:
@@ -675,14 +698,20 @@ def surrogate_leg(s_dev, d_dev, n, opt, T_ref, stream, fraction=4, reps=3):
                 "work": st}
     return {"parts": len(cuts) - 1, "part_bytes_bound": budget, "lists_bytes": 4 * m,
             "largest_part_bytes": int(4 * slices.max()), "plan_ms": plan_ms,
-            "host_lists": host, "device_lists": dev, "device_lists_one_part": one,
+            "host_lists": dict(host, per_part=parts_equal),
+            "host_lists_work_and_size_cuts": dict(host_both, parts=len(both) - 1, largest_part_bytes=int(4 * bs.max()),
+                                                  per_part=parts_both,
+                                                  cuts="tc_surrogate_plan_both: bounded in work (Sec. IV-F cost, "
+                                                       "%d parts) and in size (the byte bound) at once" % (len(cuts) - 1)),
+            "device_lists": dev, "device_lists_one_part": one,
             "device_lists_work_balanced_cuts": dict(work, largest_part_bytes=int(4 * ws.max())),
             "h2d_bytes_per_count": int(4 * sum(int(o[b]) - (int(o[a]) & ~3) for a, b in zip(cuts[:-1], cuts[1:]))),
             "roofline": roofline,
             "note": "tc_count_surrogate: parts counted one after another, each part's slice copied in "
                     "(the next copy overlapping this count), every list read in place as a message; "
                     "value = m_hat / ms of one call, CUDA events on its stream, best of %d after a warm-up; "
-                    "h2d_bytes_per_count counts the slice copies only (messages are read in place)" % reps}
+                    "per_part: each receiving part counted alone; h2d_bytes_per_count counts the slice copies "
+                    "only (messages are read in place)" % reps}
 
 
 def run_reference_batch(args):

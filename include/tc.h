@@ -443,6 +443,27 @@ tc_status tc_surrogate_plan(const int64_t* off, const int32_t* cols, int32_t n, 
                             int32_t nparts, int64_t part_bytes, int32_t max_parts, tc_stream_t stream, int32_t* cuts,
                             int32_t* nparts_out);
 
+/*
+ * Cuts bounded in work and in size at once (Sec. IV-B with the cost of Sec. IV-F, and Sec. IV's
+ * memory bound): the union of the cuts of work_parts parts of equal cost `fn` (as
+ * tc_surrogate_plan with nparts = work_parts) and the cuts of the fewest parts of equal size whose
+ * slices fit part_bytes (as tc_surrogate_plan with TC_FN_LIST and nparts = 0).  Every part lies
+ * inside one part of each, so its cost is at most 1 / work_parts of the total plus one vertex's
+ * cost, and its slice at most part_bytes.  Equal-size cuts alone can leave most of the work in
+ * one part (the part holding the hubs); equal-work cuts alone can make one slice large.
+ *   fn, off, cols, n, m  as for tc_surrogate_plan.
+ *   work_parts  1 .. TC_SURROGATE_MAX_PARTS.
+ *   part_bytes  > 0; max_parts bounds the equal-size part count (1 .. TC_SURROGATE_MAX_PARTS).
+ *   cuts        host, receives P + 1 int32, strictly increasing except for n = 0 (capacity
+ *               work_parts + max_parts + 1).
+ *   nparts_out  host; receives P (at most work_parts + the equal-size part count).
+ * Errors: as tc_surrogate_plan; TC_ERR_BUDGET also when P would exceed TC_SURROGATE_MAX_PARTS.
+ * Synchronises `stream`.
+ */
+tc_status tc_surrogate_plan_both(const int64_t* off, const int32_t* cols, int32_t n, int64_t m, int32_t fn,
+                                 int32_t work_parts, int64_t part_bytes, int32_t max_parts, tc_stream_t stream,
+                                 int32_t* cuts, int32_t* nparts_out);
+
 /* ------------------------------------------------------------------ batch */
 
 /*

@@ -306,6 +306,23 @@ def surrogate_plan(off, cols, nparts: int = 0, part_bytes: int = 0, fn: int = TC
     return cuts[:P.value + 1].copy()
 
 
+def surrogate_plan_both(off, cols, work_parts: int, part_bytes: int, fn: int = TC_FN_NEW,
+                        max_parts: int = _lib.TC_SURROGATE_MAX_PARTS, stream=None):
+    """Cuts (int32 numpy array of P + 1 vertex ids) bounded in work and size at once: the union of
+    the cuts of `work_parts` parts of equal cost `fn` and of the fewest equal-size parts whose list
+    slices each fit in part_bytes."""
+    import numpy as np
+    op, n1, ko = _array_ptr(off, "int64")
+    cp, m, kc = _array_ptr(cols, "int32")
+    cuts = np.zeros(int(work_parts) + int(max_parts) + 1, np.int32)
+    P = ctypes.c_int32()
+    rc = load().tc_surrogate_plan_both(op, cp, n1 - 1, m, int(fn), int(work_parts), int(part_bytes), int(max_parts),
+                                       _stream(stream), cuts.ctypes.data_as(ctypes.c_void_p), ctypes.byref(P))
+    del ko, kc
+    _lib.check(rc, "tc_surrogate_plan_both")
+    return cuts[:P.value + 1].copy()
+
+
 def count_surrogate(off, cols, cuts, part_lo: int = 0, part_hi: int | None = None,
                     options: _lib.Options | None = None, stream=None, stats: bool = False):
     """(total, table) of the count over the non-overlapping partition `cuts` (Sec. IV):

@@ -143,6 +143,8 @@ SIGNATURES = {
                                           ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(SurrogateStats)]),
     "tc_surrogate_plan": (ctypes.c_int, [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int64, ctypes.c_int32, P, P, ctypes.POINTER(ctypes.c_int32)]),
+    "tc_surrogate_plan_both": (ctypes.c_int, [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int64, ctypes.c_int32, P, P, ctypes.POINTER(ctypes.c_int32)]),
     "tc_batch_build": (ctypes.c_int, [P, P, P, P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(Options), P,
                                       ctypes.POINTER(P)]),
     "tc_batch_run": (ctypes.c_int, [P, P, P]),

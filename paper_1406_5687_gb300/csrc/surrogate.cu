@@ -1045,6 +1045,42 @@ tc_status tc_surrogate_plan(const int64_t* off, const int32_t* cols, int32_t n, 
     return r;
 }
 
+tc_status tc_surrogate_plan_both(const int64_t* off, const int32_t* cols, int32_t n, int64_t m, int32_t fn,
+                                 int32_t work_parts, int64_t part_bytes, int32_t max_parts, tc_stream_t stream,
+                                 int32_t* cuts, int32_t* nparts_out) {
+    if (!off || !cuts || !nparts_out || n < 0 || m < 0 || (m > 0 && !cols)) return TC_ERR_INVALID_ARG;
+    if (fn < TC_FN_ONE || fn > TC_FN_LIST) return TC_ERR_INVALID_ARG;
+    if (n == INT32_MAX) return TC_ERR_UNSUPPORTED;
+    if (work_parts < 1 || work_parts > TC_SURROGATE_MAX_PARTS || part_bytes <= 0 || max_parts < 1 ||
+        max_parts > TC_SURROGATE_MAX_PARTS)
+        return TC_ERR_INVALID_ARG;
+    *nparts_out = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int32_t> cw((size_t)work_parts + 1), cb((size_t)max_parts + 1);
+    int32_t pw = 0, pb = 0;
+    tc_status r = surrogate_plan(off, cols, n, m, fn, work_parts, 0, work_parts, s, cw.data(), &pw);
+    if (r == TC_OK) r = surrogate_plan(off, cols, n, m, TC_FN_LIST, 0, part_bytes, max_parts, s, cb.data(), &pb);
+    if (r != TC_OK) {
+        (void)cudaGetLastError();
+        return r;
+    }
+    // the union of both cut sets: every part lies inside one part of each
+    std::vector<int32_t> u;
+    u.reserve((size_t)pw + pb + 2);
+    size_t i = 0, j = 0;
+    while (i <= (size_t)pw || j <= (size_t)pb) {
+        int32_t x;
+        if (j > (size_t)pb || (i <= (size_t)pw && cw[i] <= cb[j])) x = cw[i++];
+        else x = cb[j++];
+        if (u.empty() || x != u.back()) u.push_back(x);
+    }
+    if (u.size() == 1) u.push_back(u[0]);  // n = 0: one empty part
+    if ((int64_t)u.size() - 1 > TC_SURROGATE_MAX_PARTS) return TC_ERR_BUDGET;
+    std::memcpy(cuts, u.data(), u.size() * sizeof(int32_t));
+    *nparts_out = (int32_t)u.size() - 1;
+    return TC_OK;
+}
+
 tc_status tc_count_surrogate(const int64_t* off, const int32_t* cols, int32_t n, int64_t m, const int32_t* cuts,
                              int32_t nparts, int32_t part_lo, int32_t part_hi, const tc_options* opt,
                              tc_stream_t stream, uint64_t* table, uint64_t* total, tc_surrogate_stats* stats) {

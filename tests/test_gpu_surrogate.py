@@ -192,6 +192,35 @@ def test_plan_matches_oracle_cuts(name, fn):
             assert e.value.code == _lib.TC_ERR_BUDGET
 
 
+@pytest.mark.parametrize("name", ["er_20k", "cl_200k", "star_matching", "dense_1400"])
+@pytest.mark.parametrize("work_parts", [1, 3, 5, 17])
+def test_plan_both_is_the_union_of_oracle_cuts(name, work_parts):
+    """Cuts bounded in work and in size: the union of the oracle's equal-work cuts (Sec. IV-F
+    cost) and of its fewest equal-size cuts within the byte bound; every part then satisfies both
+    bounds, and the partition still counts every triangle once."""
+    csr = CSR[name]
+    budget = max(4 * int(csr.dhat.max()), 4 * csr.m_hat // 4)
+    fw = oracle.vertex_cost(csr, oracle.COST_NEW)
+    fl = np.diff(csr.off).astype(np.uint64)
+    cw = oracle.balanced_cuts(fw, work_parts)
+    cb = None
+    for Q in range(max(1, -(-4 * csr.m_hat // budget)), 201):
+        c = oracle.balanced_cuts(fl, Q)
+        if 4 * int(np.max(csr.off[c[1:]] - csr.off[c[:-1]])) <= budget:
+            cb = c
+            break
+    assert cb is not None
+    want = np.unique(np.concatenate([cw, cb]))
+    got = tc.surrogate_plan_both(csr.off, csr.cols, work_parts, budget, max_parts=200)
+    assert np.array_equal(got, want)
+    wp = np.concatenate([[0], np.cumsum(fw.astype(np.int64))])
+    work = wp[got[1:]] - wp[got[:-1]]
+    assert int(work.max()) <= -(-int(wp[-1]) // work_parts) + int(fw.max())
+    assert 4 * int(np.max(csr.off[got[1:]] - csr.off[got[:-1]])) <= budget
+    T, _ = tc.count_surrogate(csr.off, csr.cols, got)
+    assert T == oracle.count(csr)
+
+
 def test_plan_budget_too_small():
     csr = CSR["wheel_1000"]
     with pytest.raises(_lib.TcError) as e:
