@@ -40,6 +40,10 @@ constexpr uint32_t kHashMul = 0x9E3779B1u;  // Knuth's multiplicative constant, 
 #define TC_UNITS 4
 #endif
 constexpr int kUnits = TC_UNITS;  // 16-byte units of partner lists a lane loads per step of warp_batch_count
+#ifndef TC_COUNT_MINB
+#define TC_COUNT_MINB 2
+#endif
+constexpr int kCountMinBlocks = TC_COUNT_MINB;  // resident 512-thread blocks per SM the count kernels' registers allow
 
 struct CountArgs {
     const int64_t* off;
@@ -972,7 +976,7 @@ __device__ __forceinline__ void extra_init(const CountArgs& a, int slots) {
 
 // Small owners: one worker per block, a table per warp.  MULTI: the packs of a batch.
 template <bool EXTRA, bool MULTI>
-__global__ void __launch_bounds__(512, 2) k_count_small(CountArgs a) {
+__global__ void __launch_bounds__(512, kCountMinBlocks) k_count_small(CountArgs a) {
     __shared__ unsigned s_claim;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t* tbl = smem_dyn + (size_t)warp * a.table_slots;
@@ -998,7 +1002,7 @@ __global__ void __launch_bounds__(512, 2) k_count_small(CountArgs a) {
 
 // Big owners: one worker per block, one table per block.  MULTI: the packs of a batch.
 template <bool EXTRA, bool MULTI>
-__global__ void __launch_bounds__(512, 2) k_count_big(CountArgs a) {
+__global__ void __launch_bounds__(512, kCountMinBlocks) k_count_big(CountArgs a) {
     uint32_t* smem_tbl = smem_dyn;
     __shared__ BigWindow s_win;
     __shared__ unsigned s_next;
