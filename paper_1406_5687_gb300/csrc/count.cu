@@ -458,6 +458,10 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
         if (lane == 0 && tot) atomicAdd(a.streamed, (unsigned long long)tot);
     }
     uint32_t* thits = EXTRA ? warp_task_hits(a) : nullptr;
+    // per-vertex / per-edge: this lane's hits of its current list, added to the list's task counter
+    // when the lane moves on (a lane's units come in increasing order, so its lists do too)
+    int cur_q = 0;
+    uint32_t cur_h = 0;
     const uint32_t units = len != 0u ? (((ps & 3u) + len + 3u) >> 2) : 0u;
     const uint32_t uincl = warp_inclusive_scan(units, lane);
     const uint32_t ustart = uincl - units;
@@ -523,11 +527,17 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
                     }
                 }
                 cnt += h;
-                if (h) atomicAdd(&thits[qk[u]], h);
+                if (qk[u] != cur_q) {
+                    if (cur_h) atomicAdd(&thits[cur_q], cur_h);
+                    cur_q = qk[u];
+                    cur_h = 0;
+                }
+                cur_h += h;
             }
         }
     }
     if (EXTRA) {
+        if (cur_h) atomicAdd(&thits[cur_q], cur_h);
         // each task's hits to its owner, its partner and its oriented edge, once per batch
         __syncwarp();
         const uint32_t th = lane < na ? thits[lane] : 0u;

@@ -140,6 +140,45 @@ def test_per_vertex_and_per_edge(built, name):
     assert np.array_equal(cc, want)
 
 
+def _hub_fan(k, L):
+    """A clique on {0} + W (W = 1..k), L leaves each adjacent to 0 and 1, and pendants that
+    lift every vertex of W above vertex 0 in the degree order (deg 0 = k + L)."""
+    iu = np.triu_indices(k + 1, 1)
+    s = [iu[0], np.arange(k + 1, k + 1 + L), np.arange(k + 1, k + 1 + L)]
+    d = [iu[1], np.zeros(L, np.int64), np.ones(L, np.int64)]
+    nxt = k + 1 + L
+    for w, extra in [(1, 1)] + [(j, L + 1) for j in range(2, k + 1)]:
+        s.append(np.full(extra, w, np.int64))
+        d.append(np.arange(nxt, nxt + extra))
+        nxt += extra
+    return nxt, np.concatenate(s).astype(np.int32), np.concatenate(d).astype(np.int32)
+
+
+@pytest.mark.parametrize("k,piece", [(3, 2048), (257, 256)])
+def test_per_vertex_many_hits_at_one_slot(k, piece):
+    """Vertex 0 owns all the L = 70,000 leaf tasks (its list W is longer than a leaf's {0, 1}),
+    each finding the triangle (0, leaf, 1) at vertex 1's slot of 0's table: 70,000 hits at one
+    slot (more than 16 bits hold), all in one chunk (every owner big, no static share, one
+    guided chunk).  k = 3 stages 0's list in a window of owners; k = 257 with pieces of 256
+    entries stages it in two pieces.  Closed forms: T = C(k+1, 3) + L; T_0 = T_1 = C(k, 2) + L,
+    T_w = C(k, 2) for the rest of W, 1 per leaf, 0 per pendant."""
+    L = 70000
+    n, s, d = _hub_fan(k, L)
+    opt = tc.default_options(small_max=0, piece=piece, static_percent=0, min_chunk=1 << 60)
+    ck2, ck3 = k * (k - 1) // 2, (k + 1) * k * (k - 1) // 6
+    with tc.Graph.build(s, d, n, opt) as g:
+        assert g.info()["tasks"] > g.info()["tasks_small"]
+        T, tv = g.count_per_vertex()
+        assert T == ck3 + L
+        tv = tv.cpu().numpy()
+        assert tv[0] == ck2 + L and tv[1] == ck2 + L
+        assert (tv[2:k + 1] == ck2).all()
+        assert (tv[k + 1:k + 1 + L] == 1).all()
+        assert not tv[k + 1 + L:].any()
+        T2, pe = g.count_per_edge()
+        assert T2 == T and int(pe.sum().item()) == T
+
+
 @pytest.mark.parametrize("name", ["wheel_1000", "er_20k", "cl_200k", "cl_dense"])
 @pytest.mark.parametrize("fn", [tc.TC_FN_ONE, tc.TC_FN_DEGREE, tc.TC_FN_PATRIC, tc.TC_FN_NEW])
 def test_vertex_cost(built, name, fn):
