@@ -73,8 +73,9 @@ __global__ void k_scan_single_block(uint64_t* v, int64_t n) {
 // LSD radix sort with 8-bit digits and one kernel per digit (the "onesweep" arrangement of
 // Adinets and Merrill, 2022).  The digit counts of every pass are known before the first
 // pass (gathered by the kernel that wrote the keys, or by one counting pass).  Each digit
-// pass takes tiles of 4096 keys in the order blocks start (an atomic tile counter), ranks
-// the tile's keys stably within each warp (lanes with equal digits found by eight ballots),
+// pass takes tiles of 8192 keys in the order blocks start (an atomic tile counter), ranks
+// the tile's keys stably within each warp (lanes with equal digits found through a shared
+// word of peer bits per digit),
 // publishes the tile's count of each digit, and obtains the count of each digit in all
 // earlier tiles by a decoupled look-back over their published words (flag in the top two
 // bits: aggregate of the tile alone, or inclusive prefix; then a 6-bit pass tag, so one
@@ -82,17 +83,20 @@ __global__ void k_scan_single_block(uint64_t* v, int64_t n) {
 // contiguously.  A tile waits only on tiles taken earlier, whose blocks are already running;
 // every wait is bounded and sets the error word when it gives up.
 //
-// The pass is bound by instruction issue, so the work per key is kept small: one digit
-// extraction per phase, ranks packed two to a register, full tiles without bounds checks, and
-// per (warp, digit) one shared word that turns a rank into the key's position in the tile.
+// The pass is bound by its work inside the SM (ranking, the shared-memory scatter of the
+// tile, instruction issue) more than by its 16 bytes of traffic per key, so the work per key
+// is kept small: one digit extraction per phase, ranks packed two to a register, full tiles
+// without bounds checks, per (warp, digit) one shared word that turns a rank into the key's
+// position in the tile, and tiles of 8192 keys, which halve the per-tile work of the digit
+// phase and the look-back against 4096.
 
 // Tile shape: 256 threads (one per digit in the per-digit phase), keys per thread, and the
 // blocks per SM the register budget is sized for.
 #ifndef TC_OS_ITEMS
-#define TC_OS_ITEMS 16
+#define TC_OS_ITEMS 32
 #endif
 #ifndef TC_OS_MINB
-#define TC_OS_MINB 4
+#define TC_OS_MINB 2
 #endif
 #ifndef TC_OS_RANK
 #define TC_OS_RANK 1  // 0: eight ballots per key; 1: shared peer words
