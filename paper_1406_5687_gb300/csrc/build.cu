@@ -190,7 +190,14 @@ __global__ void __launch_bounds__(kCpBlock) k_dedupe_degree(const uint64_t* __re
         if (keep && edge && lane != h) atomicAdd(&deg[a], end - lane + ((lane == 0 && continues) ? cc : 0));
         cc = open ? 32 - h + ((h == 0 && continues) ? cc : 0) : 0;
         cv = open ? a31 : 0xFFFFFFFFu;
-        if (real && !keep) atomicSub(&deg[(uint32_t)(x[k] & mask)], 1);  // a repeat, counted by the sort
+        // repeats, counted by the sort: a run of them in the row is one key repeated (each equals
+        // the key before it), taken back from its larger endpoint with one atomic per run
+        const unsigned rb = __ballot_sync(kFull, real && !keep);
+        if (((rb >> lane) & 1u) && (lane == 0 || !((rb >> (lane - 1)) & 1u))) {
+            const unsigned rafter = ~rb & ~lanemask_le();
+            const int rend = rafter ? __ffs(rafter) - 1 : 32;
+            atomicSub(&deg[(uint32_t)(x[k] & mask)], rend - lane);
+        }
     }
     if (cc > 0 && lane == 0) atomicAdd(&deg[cv], cc);
     __shared__ uint32_t ws[kCpBlock / 32];
@@ -362,25 +369,26 @@ __global__ void k_task_keys(const uint64_t* __restrict__ okeys, int64_t mh, int 
     }
 }
 
-// First task of each big-class owner: t in [Ts, T) where the owner changes.
+// First task of each big-class owner.  The records kernel writes it at the owner's number
+// (start[num] = t where the owner number changes, t >= Ts); the numbers that got one are then
+// compacted in number order, which is the big class's task order.
 struct OwnerStartPred {
-    const TaskRec* rec;
-    int64_t Ts;
-    __device__ bool operator()(int64_t i) const {
-        const int64_t t = Ts + i;
-        return t == Ts || rec[t].owner != rec[t - 1].owner;
-    }
+    const uint32_t* start;
+    __device__ bool operator()(int64_t i) const { return start[i] != 0xFFFFFFFFu; }
 };
 struct OwnerStartVal {
-    int64_t Ts;
-    __device__ uint32_t operator()(int64_t i) const { return (uint32_t)(Ts + i); }
+    const uint32_t* start;
+    __device__ uint32_t operator()(int64_t i) const { return start[i]; }
 };
 
-__global__ void k_task_records(const uint64_t* __restrict__ tkeys, int64_t T, const uint32_t* __restrict__ inv,
-                               const int64_t* __restrict__ off, TaskRec* __restrict__ rec) {
+__global__ void k_task_records(const uint64_t* __restrict__ tkeys, int64_t T, int64_t Ts,
+                               const uint32_t* __restrict__ inv, const int64_t* __restrict__ off,
+                               TaskRec* __restrict__ rec, uint32_t* __restrict__ start) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
         uint64_t k = tkeys[t];
-        uint32_t o = inv[(uint32_t)(k >> 32)], p = (uint32_t)(k & 0xFFFFFFFFu);
+        const uint32_t num = (uint32_t)(k >> 32);
+        if (t >= Ts && (t == Ts || (uint32_t)(tkeys[t - 1] >> 32) != num)) start[num] = (uint32_t)t;
+        uint32_t o = inv[num], p = (uint32_t)(k & 0xFFFFFFFFu);
         int64_t s = off[p], e = off[p + 1];
         TaskRec r;
         r.owner = o;
@@ -599,8 +607,13 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     TC_TRY(radix_sort_u64(free_buf, osorted, mh, 32, task_bits, al, s, &tsorted, g->status, spin,
                           mh > 0 ? ucounts : nullptr));
     TC_TRY(check_device_error(g, s));
+    // owner numbers run over [0, n]; start[num] receives the first task of big owner num
+    DevBuf<uint32_t> start;
+    TC_TRY(start.alloc(al, (size_t)n + 1, s));
+    TC_CUDA_TRY(cudaMemsetAsync(start.ptr, 0xFF, sizeof(uint32_t) * ((size_t)n + 1), s));
     if (T > 0) {
-        k_task_records<<<grid_stride_blocks(T), kThreads, 0, s>>>(tsorted, T, inv.ptr, off.ptr, rec.ptr);
+        k_task_records<<<grid_stride_blocks(T), kThreads, 0, s>>>(tsorted, T, (int64_t)hc.tasks_small, inv.ptr,
+                                                                   off.ptr, rec.ptr, start.ptr);
         note_launch();
     }
     TC_CUDA_TRY(cudaGetLastError());
@@ -613,7 +626,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         DevBuf<uint32_t> of;
         TC_TRY(of.alloc(al, (size_t)(nb + 1), s));
         uint64_t k = 0;
-        TC_TRY(compact(OwnerStartPred{rec.ptr, g->tasks_small}, OwnerStartVal{g->tasks_small}, nb, of.ptr, al, s, &k));
+        TC_TRY(compact(OwnerStartPred{start.ptr}, OwnerStartVal{start.ptr}, (int64_t)n + 1, of.ptr, al, s, &k));
         const uint32_t endv = (uint32_t)T;
         TC_CUDA_TRY(cudaMemcpyAsync(of.ptr + k, &endv, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
         TC_CUDA_TRY(cudaStreamSynchronize(s));
