@@ -701,6 +701,7 @@ __device__ void process_small_block(const CountArgs& a, long long t0, long long 
 // ------------------------------------------------------------------ big owners: one block each
 
 constexpr int kWinOwners = 32;
+constexpr int kStageItems = 4;  // list entries a thread loads before inserting them
 
 // A window of consecutive big owners staged together into regions of the block's table.
 struct BigWindow {
@@ -710,10 +711,24 @@ struct BigWindow {
     uint32_t reg[kWinOwners];         // owner i's table region
     uint32_t lmin[kWinOwners];        // owner i's first and last list entry
     uint32_t lmax[kWinOwners];
+    uint32_t epre[kWinOwners + 1];    // list entries of the owners before owner i (then the total)
     long long k;                      // owner index of the window's first owner
     uint32_t used;                    // table slots in use
     int nown;                         // owners in the window; 0: one owner needs several pieces
 };
+
+// A warp's next batch of 32 tasks of the block's task range [t, tend) (s_next: tasks claimed
+// so far).  Returns the batch's size (0: the range is done).  (Smaller batches near the end of
+// the range, to even out the warps' arrival at the barrier after it, measured slower: a batch
+// has a fixed cost of record loads, trims and scans.)
+__device__ __forceinline__ int claim_batch(unsigned* s_next, long long t, long long tend, int lane, long long& tb) {
+    unsigned b = 0;
+    if (lane == 0) b = atomicAdd(s_next, 32u);
+    b = __shfl_sync(kFull, b, 0);
+    tb = t + (long long)b;
+    if (tb >= tend) return 0;
+    return (int)(tend - tb < 32 ? tend - tb : 32);
+}
 
 // Count the tasks [t, tend) of one owner whose list (cols[ob, ob + ol)) is longer than a
 // piece: the table holds one piece at a time and every partner list is streamed per piece.
@@ -729,16 +744,23 @@ __device__ void big_owner_pieces(const CountArgs& a, long long t, long long tend
         for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) tbl[i] = kEmpty;
         if (threadIdx.x == 0) *s_next = 0;
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < pl; i += blockDim.x) hash_insert(hv, (uint32_t)__ldg(&a.cols[ob + ps + i]));
+        for (uint32_t i0 = threadIdx.x; i0 < pl; i0 += kStageItems * blockDim.x) {
+            uint32_t xs[kStageItems];  // each thread's entries loaded before any is inserted
+#pragma unroll
+            for (int k = 0; k < kStageItems; ++k) {
+                const uint32_t i = i0 + (uint32_t)k * blockDim.x;
+                xs[k] = i < pl ? (uint32_t)__ldg(&a.cols[ob + ps + i]) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < kStageItems; ++k)
+                if (i0 + (uint32_t)k * blockDim.x < pl) hash_insert(hv, xs[k]);
+        }
         const uint32_t pmin = (uint32_t)__ldg(&a.cols[ob + ps]), pmax = (uint32_t)__ldg(&a.cols[ob + ps + pl - 1]);
         __syncthreads();
         for (;;) {
-            unsigned b = 0;
-            if (lane == 0) b = atomicAdd(s_next, 1u);
-            b = __shfl_sync(kFull, b, 0);
-            const long long tb = t + (long long)b * 32;
-            if (tb >= tend) break;
-            const int nb = (int)(tend - tb < 32 ? tend - tb : 32);
+            long long tb;
+            const int nb = claim_batch(s_next, t, tend, lane, tb);
+            if (nb == 0) break;
             TaskRec r = {0u, 0u, 0u, 0u};
             if (lane < nb) r = a.tasks[tb + lane];
             warp_batch<EXTRA, true>(a, r, nb, tbl, reg, pmin, pmax, lane, acc);
@@ -792,6 +814,9 @@ __device__ void process_big(const CountArgs& a, long long t0, long long t1, uint
             const unsigned fit = __ballot_sync(kFull, exists && cend <= (uint32_t)a.table_slots);
             const int nown = fit == kFull ? 32 : __ffs(~fit) - 1;  // leading run of owners that fit
             const uint32_t used = __shfl_sync(kFull, cend, (nown - 1) & 31);
+            const uint32_t eincl = warp_inclusive_scan(lane < nown ? ol : 0u, lane);
+            if (lane < nown) w->epre[lane] = eincl - ol;
+            if (lane == 31) w->epre[nown] = eincl;  // nown <= 32: the window's entries
             if (lane < (nown > 0 ? nown : 1)) {
                 w->first[lane] = lane == 0 ? t : first;
                 w->ob[lane] = ob;
@@ -818,20 +843,32 @@ __device__ void process_big(const CountArgs& a, long long t0, long long t1, uint
             for (uint32_t i = threadIdx.x; i < used; i += blockDim.x) tbl[i] = kEmpty;
             if (threadIdx.x == 0) *s_next = 0;
             __syncthreads();
-            for (int i = warp; i < nown; i += nwarps) {
-                const HashView hv = region_view(tbl, w->reg[i]);
-                const long long ob = w->ob[i];
-                const uint32_t ol = w->ol[i];
-                for (uint32_t e = lane; e < ol; e += 32) hash_insert(hv, (uint32_t)__ldg(&a.cols[ob + e]));
+            // stage the window's lists: its entries numbered one after another and spread over
+            // the block's threads, each thread's entries loaded before any is inserted
+            const uint32_t etot = w->epre[nown];
+            for (uint32_t e0 = threadIdx.x; e0 < etot; e0 += kStageItems * blockDim.x) {
+                uint32_t xs[kStageItems];
+                int oi[kStageItems];
+#pragma unroll
+                for (int k = 0; k < kStageItems; ++k) {
+                    const uint32_t e = e0 + (uint32_t)k * blockDim.x;
+                    int lo = 0, hi = nown - 1;  // the last owner whose entries start at or before e
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (w->epre[mid] <= e) lo = mid; else hi = mid - 1;
+                    }
+                    oi[k] = lo;
+                    xs[k] = e < etot ? (uint32_t)__ldg(&a.cols[w->ob[lo] + (e - w->epre[lo])]) : 0u;
+                }
+#pragma unroll
+                for (int k = 0; k < kStageItems; ++k)
+                    if (e0 + (uint32_t)k * blockDim.x < etot) hash_insert(region_view(tbl, w->reg[oi[k]]), xs[k]);
             }
             __syncthreads();
             for (;;) {
-                unsigned b = 0;
-                if (lane == 0) b = atomicAdd(s_next, 1u);
-                b = __shfl_sync(kFull, b, 0);
-                const long long tb = t + (long long)b * 32;
-                if (tb >= tend) break;
-                const int nb = (int)(tend - tb < 32 ? tend - tb : 32);
+                long long tb;
+                const int nb = claim_batch(s_next, t, tend, lane, tb);
+                if (nb == 0) break;
                 TaskRec r = {0u, 0u, 0u, 0u};
                 uint32_t reg = 0u, omin = 0u, omax = 0u;
                 if (lane < nb) {
