@@ -39,6 +39,7 @@ constexpr uint32_t kHashMul = 0x9E3779B1u;  // Knuth's multiplicative constant, 
 #ifndef TC_UNITS
 #define TC_UNITS 4
 #endif
+constexpr int kStageItems = 4;  // list entries a thread loads before inserting them (staging)
 constexpr int kUnits = TC_UNITS;  // 16-byte units of partner lists a lane loads per step of warp_batch_count
 #ifndef TC_COUNT_MINB
 #define TC_COUNT_MINB 2
@@ -644,17 +645,26 @@ __device__ void process_small(const CountArgs& a, long long t0, long long t1, ui
         const uint32_t excl = incl - s_len;
         const uint32_t tot = __shfl_sync(kFull, incl, 31);
         uint32_t before = 0;
-        for (uint32_t base = 0; base < tot; base += 32u) {
-            const uint32_t rel = excl - base;
-            const uint32_t bit = (s_len != 0u && rel < 32u) ? (1u << rel) : 0u;
-            const uint32_t starts = __reduce_or_sync(kFull, bit);
-            const int q = ((int)(before + __popc(starts & lanemask_le())) - 1) & 31;
-            const long long obq = __shfl_sync(kFull, s_ob, q);
-            const uint32_t eq = __shfl_sync(kFull, excl, q);
-            const uint32_t rq = __shfl_sync(kFull, s_reg, q);
-            const uint32_t g = base + lane;
-            if (g < tot) hash_insert(region_view(tbl, rq), (uint32_t)__ldg(&a.cols[obq + (g - eq)]));
-            before += __popc(starts);
+        for (uint32_t base0 = 0; base0 < tot; base0 += 32u * kStageItems) {
+            // each lane's entries of kStageItems rows loaded before any is inserted
+            uint32_t xs[kStageItems], rqs[kStageItems];
+#pragma unroll
+            for (int k = 0; k < kStageItems; ++k) {
+                const uint32_t base = base0 + 32u * (uint32_t)k;
+                const uint32_t rel = excl - base;
+                const uint32_t bit = (s_len != 0u && rel < 32u) ? (1u << rel) : 0u;
+                const uint32_t starts = __reduce_or_sync(kFull, bit);
+                const int q = ((int)(before + __popc(starts & lanemask_le())) - 1) & 31;
+                const long long obq = __shfl_sync(kFull, s_ob, q);
+                const uint32_t eq = __shfl_sync(kFull, excl, q);
+                rqs[k] = __shfl_sync(kFull, s_reg, q);
+                const uint32_t g = base + lane;
+                xs[k] = g < tot ? (uint32_t)__ldg(&a.cols[obq + (g - eq)]) : 0u;
+                before += __popc(starts);
+            }
+#pragma unroll
+            for (int k = 0; k < kStageItems; ++k)
+                if (base0 + 32u * (uint32_t)k + lane < tot) hash_insert(region_view(tbl, rqs[k]), xs[k]);
         }
         __syncwarp();
         warp_batch<EXTRA, false>(a, r, nt, tbl, reg, 0u, 0xFFFFFFFFu, lane, acc);
@@ -701,7 +711,6 @@ __device__ void process_small_block(const CountArgs& a, long long t0, long long 
 // ------------------------------------------------------------------ big owners: one block each
 
 constexpr int kWinOwners = 32;
-constexpr int kStageItems = 4;  // list entries a thread loads before inserting them
 
 // A window of consecutive big owners staged together into regions of the block's table.
 struct BigWindow {
