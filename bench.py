@@ -284,7 +284,8 @@ def build_bytes(info):
     task keys: bits(n + 1)); the dedupe pass and the orienting compaction read the sorted keys
     (8 each) and write 8 per distinct edge; the lists' last pass also writes cols (4); the task
     keys read 8 and write 8 per oriented edge; the task sort's last pass writes 16-byte records
-    instead of keys; the owner index reads the records' owners (4 per task, twice)."""
+    instead of keys and each big owner's first task at its owner number; the owner index clears
+    that array of n + 1 numbers (4 each) and compacts it (read twice)."""
     m, mh, T, n = int(info["m_input"]), int(info["m_hat"]), int(info["tasks"]), int(info["n"])
     b = _bits_for(n)
     p1, p2, p3 = -(-2 * b // 8), -(-b // 8), -(-_bits_for(n + 1) // 8)
@@ -297,7 +298,7 @@ def build_bytes(info):
         "offsets": 4 * n + 8 * (n + 1),
         "task_keys": 16 * mh + 12 * n,
         "sort_tasks": 16 * (p3 - 1) * mh + 8 * mh + 16 * T + 8 * (n + 1) + 4 * n,
-        "owner_index": 8 * T,
+        "owner_index": 12 * (n + 1),
     }
     return {"bytes": sum(terms.values()), "terms": terms, "sort_passes": [p1, p2, p3],
             "sort_bytes": 16 * (p1 * m + (p2 + p3) * mh)}
