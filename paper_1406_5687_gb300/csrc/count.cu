@@ -41,6 +41,14 @@ constexpr uint32_t kHashMul = 0x9E3779B1u;  // Knuth's multiplicative constant, 
 #endif
 constexpr int kStageItems = 4;  // list entries a thread loads before inserting them (staging)
 constexpr int kUnits = TC_UNITS;  // 16-byte units of partner lists a lane loads per step of warp_batch_count
+#ifndef TC_UNITS_X
+#define TC_UNITS_X 3
+#endif
+constexpr int kUnitsX = TC_UNITS_X;  // the same for per-vertex / per-edge counts, whose per-hit path needs more registers
+#ifndef TC_UNITS_XS
+#define TC_UNITS_XS 2
+#endif
+constexpr int kUnitsXS = TC_UNITS_XS;  // ... in the small-owner kernel (3 and 2: no register spills)
 #ifndef TC_COUNT_MINB
 #define TC_COUNT_MINB 2
 #endif
@@ -468,13 +476,14 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
     const uint32_t ustart = uincl - units;
     const uint32_t U = __shfl_sync(kFull, uincl, 31);
     uint32_t before = 0;  // lists that start before the current window
-    for (uint32_t w0 = 0; w0 < U; w0 += 32u * kUnits) {
-        int4 v[kUnits];
-        uint32_t lo[kUnits], ln[kUnits], e0[kUnits], rg[kUnits];
-        int qk[kUnits];
-        bool in[kUnits];
+    constexpr int NU = EXTRA ? (TRIM ? kUnitsX : kUnitsXS) : kUnits;
+    for (uint32_t w0 = 0; w0 < U; w0 += 32u * NU) {
+        int4 v[NU];
+        uint32_t lo[NU], ln[NU], e0[NU], rg[NU];
+        int qk[NU];
+        bool in[NU];
 #pragma unroll
-        for (int u = 0; u < kUnits; ++u) {
+        for (int u = 0; u < NU; ++u) {
             const uint32_t wb = w0 + 32u * (uint32_t)u;
             const uint32_t rel = ustart - wb;
             const uint32_t bit = (units != 0u && rel < 32u) ? (1u << rel) : 0u;
@@ -492,7 +501,7 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
             v[u] = in[u] ? __ldg(reinterpret_cast<const int4*>(a.cols + e0[u])) : make_int4(-1, -1, -1, -1);
         }
 #pragma unroll
-        for (int u = 0; u < kUnits; ++u) {
+        for (int u = 0; u < NU; ++u) {
             if (w0 + 32u * (uint32_t)u >= U) break;
             const HashView hv = region_view(tbl, rg[u]);
             const uint32_t xs[4] = {(uint32_t)v[u].x, (uint32_t)v[u].y, (uint32_t)v[u].z, (uint32_t)v[u].w};
