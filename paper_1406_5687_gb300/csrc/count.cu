@@ -218,11 +218,15 @@ extern __shared__ uint32_t smem_dyn[];
 // (a count array beside the table, one shared atomic per hit) and added to T_w once per staged
 // list.  A task's hits are summed in the warp's shared counter of that task and added to its
 // owner, its partner and its edge once per batch.
-__device__ __forceinline__ long long oriented_edge_position(const CountArgs& a, uint32_t owner, uint32_t partner) {
-    // the oriented edge runs from whichever endpoint comes first in the degree order
-    const int32_t dox = a.deg[owner], dpx = a.deg[partner];
-    const bool owner_first = dox < dpx || (dox == dpx && owner < partner);
-    return edge_position(a, owner_first ? owner : partner, owner_first ? partner : owner);
+// Position of x in the sorted list cols[p, p + len), or -1.
+__device__ __forceinline__ long long list_position(const int32_t* __restrict__ cols, uint32_t p, uint32_t len,
+                                                   uint32_t x) {
+    uint32_t lo = p, hi = p + len;
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if ((uint32_t)__ldg(&cols[mid]) < x) lo = mid + 1; else hi = mid;
+    }
+    return (lo < p + len && (uint32_t)__ldg(&cols[lo]) == x) ? (long long)lo : -1ll;
 }
 
 __device__ __forceinline__ uint32_t* warp_task_hits(const CountArgs& a) {
@@ -450,6 +454,7 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
     const int na = __popc(act);
     TaskRec r = rin;
     uint32_t reg = reg_in;
+    uint32_t p0 = rin.pstart;  // per-edge counts: the untrimmed partner list is cols[p0, p0 + r.plen)
     if (TRIM && act != (na == 32 ? kFull : (1u << na) - 1u)) {
         const int src = lane < na ? nth_set_bit(act, lane) : 0;
         const uint32_t gl = __shfl_sync(kFull, len, src);
@@ -458,6 +463,8 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
         if (EXTRA) {
             r.owner = __shfl_sync(kFull, rin.owner, src);
             r.partner = __shfl_sync(kFull, rin.partner, src);
+            r.plen = __shfl_sync(kFull, rin.plen, src);
+            p0 = __shfl_sync(kFull, rin.pstart, src);
         }
         len = lane < na ? gl : 0u;
     }
@@ -558,7 +565,13 @@ __device__ __forceinline__ void warp_batch_count(const CountArgs& a, const TaskR
                 atomicAdd(&a.t_v[r.owner], (unsigned long long)th);
                 atomicAdd(&a.t_v[r.partner], (unsigned long long)th);
             }
-            if (a.per_edge) atomicAdd(&a.per_edge[oriented_edge_position(a, r.owner, r.partner)], th);
+            if (a.per_edge) {
+                // the oriented edge is partner -> owner when the owner is in the partner's list
+                // (found in the list this task streamed), else owner -> partner
+                long long pos = list_position(a.cols, p0, r.plen, r.owner);
+                if (pos < 0) pos = edge_position(a, r.owner, r.partner);
+                atomicAdd(&a.per_edge[pos], th);
+            }
         }
     }
 }
