@@ -460,6 +460,29 @@ def test_unaligned_and_ragged_device_edge_lists(shift):
     assert e.value.code == tc._lib.TC_ERR_VERTEX_RANGE
 
 
+@pytest.mark.parametrize("m", [8191, 8192, 8193, 3 * 8192 + 1, 4096 * 3 - 1])
+def test_sort_tile_boundaries(m):
+    """Edge lists of about one, two and three radix-sort tiles (8192 keys each), on either side of
+    a tile's end, with repeats, self-loops and hubs: the lists, degrees and count equal the
+    oracle's (bit-exact)."""
+    rng = np.random.default_rng(m)
+    n = 3000
+    hub = rng.integers(0, 20, size=m)                    # a few hubs take most edges
+    other = rng.integers(0, n, size=m)
+    pick = rng.random(m) < 0.5
+    s = np.where(pick, hub, other).astype(np.int32)
+    d = rng.integers(0, n, size=m).astype(np.int32)
+    d[::97] = s[::97]                                    # self-loops
+    s[1::53], d[1::53] = s[0:-1:53][: len(s[1::53])], d[0:-1:53][: len(d[1::53])]  # repeats
+    csr = oracle_csr(n, s, d)
+    with tc.Graph.build(s, d, n) as g:
+        deg, off, cols, _ = g.csr()
+        assert np.array_equal(deg.cpu().numpy(), csr.deg)
+        assert np.array_equal(off.cpu().numpy(), csr.off)
+        assert np.array_equal(cols.cpu().numpy(), csr.cols)
+        assert g.count() == oracle.count(csr)
+
+
 @pytest.mark.parametrize("name", ["cl_200k", "cl_dense", "ba_30k", "k60", "no_edges"])
 @pytest.mark.parametrize("nparts", [1, 2, 3, 7, 64])
 def test_partitioned_count_adds_up(name, nparts):
