@@ -209,7 +209,8 @@ __device__ __forceinline__ long long edge_position(const CountArgs& a, uint32_t 
     return lo;
 }
 
-// The block's dynamic shared memory: hash tables, then (per-vertex counts) the T_v cache.
+// The block's dynamic shared memory: hash tables, then (per-vertex counts) the tables' slot
+// counts, then (per-vertex / per-edge counts) the warps' task-hit counters.
 extern __shared__ uint32_t smem_dyn[];
 
 // Per-vertex and per-edge outputs.  A triangle found at task (owner, partner) with third vertex
